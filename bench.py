@@ -1,0 +1,380 @@
+"""Benchmark of the dense-CRF hot path: Frank-Wolfe iterations/s at 500x375, L=21.
+
+One step = one dcrf_qp_fw call of `--iters` Frank-Wolfe iterations over a batch
+of `--batch` synthetic VOC-shaped images (500x375, 21 labels, 30 Voronoi
+regions), lattices built beforehand (they are reused by every iteration), with
+float16 lattice storage.  value = images x iterations / second over all ranks.
+
+Also reported: the plain float32 single-image form, the end-to-end rate
+through the public API from host buffers (features, lattice builds, solver and
+copies inside the timed region), the roofline of the dominant kernel from CUDA
+events taken on the launching stream inside the timed region, the oracle timed
+on the host cores, and SM clocks sampled during the timed region.
+
+Multi-GPU: one process per GPU (torchrun); every rank solves its own batch
+(images are independent problems), so there is no data-path collective; only
+the timing uses a max-reduction over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1608_06192_gb300 import synthetic as S  # noqa: E402
+
+METRIC = "FW iters/s at 500x375, L=21 (batched FP16 vs plain FP32); % HBM roofline"
+UNIT = "image-iterations/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--iters", type=int, default=100)
+    ap.add_argument("--storage", default="f16", choices=["f16", "f32"])
+    ap.add_argument("--width", type=int, default=500)
+    ap.add_argument("--height", type=int, default=375)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# oracle (CPU) timing: the reference arm and the cpu_baseline leg
+
+def oracle_rate(iters: int, seed: int = 0):
+    """Oracle Frank-Wolfe on one 500x375 image: (image-iterations/s, seconds, threads)."""
+    try:
+        from threadpoolctl import threadpool_limits
+    except Exception:
+        threadpool_limits = None
+    if threadpool_limits is not None:
+        with threadpool_limits(1):
+            return _oracle_rate(iters, seed)
+    return _oracle_rate(iters, seed)
+
+
+def _oracle_rate(iters, seed):
+    from oracle import crf, qp
+    from oracle import permutohedral as P
+    p = S.make_problem(500, 375, 30, 21, seed)
+    fb, fs = crf.features(p.rgb, *p.thetas)
+    k = P.LatticeGaussian([crf.to_fp32_features(fb), crf.to_fp32_features(fs)], p.weights)
+    c = crf.DenseCRF(p.unaries, k)
+    qp.frank_wolfe(c, p.y0, 1)                      # warm-up
+    t0 = time.perf_counter()
+    qp.frank_wolfe(c, p.y0, iters)
+    dt = time.perf_counter() - t0
+    return iters / dt, dt, 1
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    per_step = 3
+    oracle_rate(1)
+    times = []
+    for _ in range(args.warmup):
+        oracle_rate(per_step)
+    for _ in range(args.steps):
+        r, dt, cores = oracle_rate(per_step)
+        times.append(dt)
+    total = sum(times)
+    value = args.steps * per_step / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "1 x 500x375 synthetic VOC-shaped image, L=21, oracle Frank-Wolfe (FP64 numpy)",
+                   "iters_per_step": per_step},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} FW iterations on one 500x375 image per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            return out
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if sm:
+            busy = [x for x in sm if x > 0.5 * max(sm)] or sm
+            out.update(sm_mhz=statistics.median(busy), sm_max_mhz=max(smax), reasons=sorted(reasons),
+                       samples=len(sm))
+        return out
+
+
+def algorithmic_bytes(kind, n, L, lat_m, lat_d, storage):
+    """Bytes one Frank-Wolfe iteration must move for a kernel kind (all launches of it)."""
+    Lp = 8 if L <= 8 else (24 if L <= 24 else 64)
+    esz = 2 if storage == "f16" else 4
+    if kind == "fw_pixel":
+        per_px = 12 * L + 6 + sum(8 * (d + 1) for d in lat_d)
+        return n * per_px + sum(m * Lp * (4 + esz + 4) for m in lat_m)
+    if kind == "blur_pass":
+        return sum((d + 1) * (m * Lp * (2 * esz) + 8 * m) + m * Lp * (4 - esz) for m, d in zip(lat_m, lat_d))
+    if kind == "fw_latdot":
+        return sum(m * Lp * (8 + esz) for m in lat_m)
+    if kind == "fw_latupd":
+        return sum(m * Lp * (20 + esz) + 4 * m for m in lat_m)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+    from paper_1608_06192_gb300 import _abi as D, build
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    dev = torch.device("cuda", local)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    stream = torch.cuda.Stream(device=dev)
+    B, T, W_, H_ = args.batch, args.iters, args.width, args.height
+    probs = [S.make_problem(W_, H_, 30, 21, seed=1000 * rank + i) for i in range(B)]
+    L = 21
+    n = sum(p.n_pixels for p in probs)
+    rgb_h = torch.from_numpy(np.concatenate([p.rgb.reshape(-1, 3) for p in probs])).pin_memory()
+    phi_h = torch.from_numpy(np.concatenate([p.unaries for p in probs])).pin_memory()
+    y0_h = torch.from_numpy(np.concatenate([p.y0 for p in probs])).pin_memory()
+    widths, heights = [p.width for p in probs], [p.height for p in probs]
+    off = np.concatenate([[0], np.cumsum([p.n_pixels for p in probs])]).astype(np.int64)
+    th, wts = probs[0].thetas, probs[0].weights
+
+    with torch.cuda.stream(stream):
+        rgb = rgb_h.to(dev, non_blocking=True)
+        phi = phi_h.to(dev, non_blocking=True)
+        y0 = y0_h.to(dev, non_blocking=True)
+        fb, fs = D.dcrf_features(rgb, widths, heights, *th, stream=stream)
+        t0 = time.perf_counter()
+        lb = D.dcrf_lattice_build(fb, off, stream=stream)
+        ls = D.dcrf_lattice_build(fs, off, stream=stream)
+        stream.synchronize()
+        build_s = time.perf_counter() - t0
+        Y = torch.empty_like(y0)
+
+        def step():
+            Y.copy_(y0)
+            D.dcrf_qp_fw(phi, [lb, ls], wts, Y, T, storage=args.storage, records=False, stream=stream)
+
+        for _ in range(max(3, args.warmup)):
+            step()
+        stream.synchronize()
+        if world > 1:
+            dist.barrier()
+        D.profile_enable(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(args.steps):
+                step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        prof = D.profile_read()
+        D.profile_enable(False)
+        elapsed_ms = e0.elapsed_time(e1)
+        t = torch.tensor([elapsed_ms], device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+        ms_step = elapsed_ms / args.steps
+        value = world * B * T / (ms_step / 1000.0)
+
+        # roofline of the dominant kernel (CUDA events on the launching stream)
+        lat_m, lat_d = [lb.m, ls.m], [5, 2]
+        per_iter_launch = {"fw_pixel": 1, "blur_pass": 9, "fw_latdot": 2, "fw_latupd": 2}
+        roof = None
+        kinds = {}
+        for kind, (cnt, ms) in prof.items():
+            by = algorithmic_bytes(kind, n, L, lat_m, lat_d, args.storage)
+            if by and cnt and kind in per_iter_launch:
+                per_launch = by / per_iter_launch[kind]
+                gbs = per_launch / (ms / cnt / 1000.0) / 1e9
+                kinds[kind] = {"launches": cnt, "ms": round(ms, 3), "GB/s": round(gbs, 1),
+                               "bytes_per_launch": int(per_launch), "us_per_launch": round(1000 * ms / cnt, 2)}
+            else:
+                kinds[kind] = {"launches": cnt, "ms": round(ms, 3)}
+        dom = max((k for k in kinds if "GB/s" in kinds[k]), key=lambda k: kinds[k]["ms"], default=None)
+        if dom is not None:
+            ach = kinds[dom]["GB/s"]
+            roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": round(ach / hbm_peak, 4), "peak_source": peak_src,
+                    "bytes_per_launch": kinds[dom]["bytes_per_launch"], "traffic": None}
+        launches = sum(c for c, _ in prof.values())
+
+        # plain float32, one image, no batching
+        p1 = [probs[0]]
+        n1 = p1[0].n_pixels
+        l1b = D.dcrf_lattice_build(fb[:n1].contiguous(), [0, n1], stream=stream)
+        l1s = D.dcrf_lattice_build(fs[:n1].contiguous(), [0, n1], stream=stream)
+        Y1 = torch.empty_like(y0[:n1])
+        for _ in range(3):
+            Y1.copy_(y0[:n1])
+            D.dcrf_qp_fw(phi[:n1], [l1b, l1s], wts, Y1, T, storage="f32", records=False, stream=stream)
+        stream.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        reps = 5
+        for _ in range(reps):
+            Y1.copy_(y0[:n1])
+            D.dcrf_qp_fw(phi[:n1], [l1b, l1s], wts, Y1, T, storage="f32", records=False, stream=stream)
+        a1.record(stream)
+        stream.synchronize()
+        plain_fp32 = reps * T / (a0.elapsed_time(a1) / 1000.0)
+
+        # end to end through the public API from pinned host buffers
+        e2e = None
+        if not args.no_e2e:
+            Yh = torch.empty_like(y0_h).pin_memory()
+
+            def e2e_step():
+                r = rgb_h.to(dev, non_blocking=True)
+                ph = phi_h.to(dev, non_blocking=True)
+                yy = y0_h.to(dev, non_blocking=True)
+                f1, f2 = D.dcrf_features(r, widths, heights, *th, stream=stream)
+                la = D.dcrf_lattice_build(f1, off, stream=stream)
+                lc = D.dcrf_lattice_build(f2, off, stream=stream)
+                D.dcrf_qp_fw(ph, [la, lc], wts, yy, T, storage=args.storage, records=False, stream=stream)
+                Yh.copy_(yy, non_blocking=True)
+                return la, lc
+
+            keep = e2e_step()
+            stream.synchronize()
+            b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            k = max(1, min(args.steps, 3))
+            b0.record(stream)
+            for _ in range(k):
+                keep = e2e_step()
+            b1.record(stream)
+            stream.synchronize()
+            e2e_ms = b0.elapsed_time(b1) / k
+            tt = torch.tensor([e2e_ms], device=dev)
+            if world > 1:
+                dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_ms = float(tt.item())
+            e2e = {"value": world * B * T / (e2e_ms / 1000.0), "unit": UNIT,
+                   "h2d_bytes_per_step": int(rgb_h.numel() * 4 + phi_h.numel() * 4 + y0_h.numel() * 4),
+                   "d2h_bytes_per_step": int(Yh.numel() * 4), "ms_per_step": round(e2e_ms, 3)}
+            del keep
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, dt, cores = oracle_rate(20)
+        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "20 oracle Frank-Wolfe iterations on one 500x375 image (FP64 numpy)",
+               "seconds": round(dt, 2)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"{B} x {W_}x{H_} synthetic VOC-shaped images per GPU, L=21, "
+                                   f"{args.storage} lattice storage, {T} Frank-Wolfe iterations per step",
+                       "images_per_gpu": B, "iters_per_step": T, "storage": args.storage,
+                       "pixels_per_gpu": n, "vertices": {"bilateral": lb.m, "spatial": ls.m},
+                       "l2": "inputs larger than L2 (per-pixel state of the batch is several GB)",
+                       "lattice_build_s": round(build_s, 4)},
+            "plain_fp32_single_image": {"value": plain_fp32, "unit": UNIT},
+            "roofline": roof,
+            "kernels": kinds,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

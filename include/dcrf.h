@@ -1,0 +1,205 @@
+/*
+ * dcrf.h -- C ABI of the GB300 dense-CRF filtering hot path.
+ *
+ * Efficient Continuous Relaxations for Dense CRF (Desmaison, Bunel, Kohli,
+ * Torr, Kumar; arXiv 1608.06192).  The library computes, on one GPU, the dense
+ * Gaussian pairwise product sum_b K(f_a, f_b) y_b over all label channels with
+ * a permutohedral lattice (Section 3, "Filter-based Method", Eq. 6), and the
+ * three solvers built on it: Frank-Wolfe on the convex QP relaxation (Section
+ * 4, Algorithm 1, Appendix B), CCCP on the generic DC relaxation (Section 5.1,
+ * Algorithm 2) and the LP relaxation's subgradient by sort + divide and
+ * conquer (Section 6, Eq. 19-20, Appendix E) with projected subgradient steps
+ * (Algorithm 3).
+ *
+ * Conventions for every entry point:
+ *  - Pointers documented "device" must point to GPU memory owned by the
+ *    caller (for example torch tensors), contiguous, row-major; "host"
+ *    pointers are CPU memory.  The library never frees caller memory.
+ *  - Pixels of a batch are concatenated: image b owns rows
+ *    offsets[b] .. offsets[b+1]-1.  A single image is a batch of one.
+ *  - Per-pixel label arrays are [N][L] float32, label-contiguous.
+ *  - Calls are asynchronous on the given stream unless stated otherwise; the
+ *    returned status covers argument checks and launch errors.  Errors found
+ *    on the device (hash table full, key out of range, non-finite values,
+ *    a bounded wait that expired) are recorded in a device status word of the
+ *    lattice and returned by the next call that synchronises
+ *    (dcrf_lattice_build, dcrf_lattice_status, and solver calls that copy
+ *    records to the host).
+ *  - No entry point launches work on a stream other than the one given.
+ */
+#ifndef DCRF_H
+#define DCRF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *dcrf_stream;       /* a cudaStream_t; NULL = legacy default stream */
+typedef struct dcrf_lattice_s *dcrf_lattice;   /* opaque, owned by the library */
+
+typedef enum {
+    DCRF_OK = 0,
+    DCRF_E_INVAL = -1,       /* bad argument: null pointer, size, dimension, shapes that disagree */
+    DCRF_E_NOMEM = -2,       /* device allocation failed */
+    DCRF_E_CUDA = -3,        /* a CUDA runtime call or launch failed */
+    DCRF_E_TABLE_FULL = -4,  /* lattice hash table ran out of slots (bounded probing) */
+    DCRF_E_KEY_RANGE = -5,   /* a lattice coordinate does not fit the packed key */
+    DCRF_E_TIMEOUT = -6,     /* a bounded device-side wait gave up */
+    DCRF_E_NONFINITE = -7    /* NaN or Inf met in inputs or a reduction */
+} dcrf_status;
+
+typedef enum {
+    DCRF_STORAGE_F32 = 0,    /* lattice values stored in float32 */
+    DCRF_STORAGE_F16 = 1     /* lattice values stored in float16, accumulated in float32 */
+} dcrf_storage;
+
+/* One Frank-Wolfe iteration of one image (Algorithm 1; Appendix B). */
+typedef struct {
+    double energy;   /* S_cvx(y^t) of Eq. 10 (or the CCCP inner objective) before the step */
+    double gap;      /* <g, y^t - s>, g = (phi - d) + 2 (Psi + D) y^t  (Eq. 12, Eq. 14) */
+    double alpha;    /* step taken, the minimiser over [0,1] of A a^2 + B a */
+    double A;        /* (s - y)^T (Psi + D) (s - y) */
+    double B;        /* derivative of the evaluated quadratic at a = 0 */
+} dcrf_fw_record;
+
+const char *dcrf_status_string(int status);
+int dcrf_version(void);
+
+/*
+ * Step a1 -- features of Appendix G (kernel form of Eq. 4).
+ * rgb: device [N][3] float32, the images of the batch concatenated, each
+ *   row-major (pixel a = y*W + x).  widths, heights: host [batch].
+ * f_bil: device [N][5] = (x/theta_alpha, y/theta_alpha, rgb/theta_beta).
+ * f_sp:  device [N][2] = (x, y)/theta_gamma.  Either output may be NULL.
+ * Each value is one correctly rounded float32 division.
+ */
+dcrf_status dcrf_features(const float *rgb, const int32_t *widths, const int32_t *heights, int batch,
+                          float theta_alpha, float theta_beta, float theta_gamma,
+                          float *f_bil, float *f_sp, dcrf_stream stream);
+
+/*
+ * Step a2 -- permutohedral lattice of one Gaussian kernel (Section 3 and
+ * Appendix A of the paper, which cites Adams et al. for the method).
+ * features: device [N][d] float32, already divided by the kernel widths, so
+ *   that the kernel is exp(-|f_a - f_b|^2 / 2).  1 <= d <= 8.
+ * offsets: host [batch+1], offsets[0] = 0, offsets[batch] = N; each image
+ *   gets its own lattice (points of different images never interact).
+ * On success *out owns the device arrays of the lattice: enclosing simplex
+ * of every point (vertex ids and barycentric weights), vertex keys, blur
+ * neighbours and K~1 (the filtered ones vector).  The build synchronises the
+ * stream once (to read the vertex count) and returns DCRF_E_TABLE_FULL or
+ * DCRF_E_KEY_RANGE when the device reported it; *out is then NULL.
+ * A lattice is immutable after the build and may be read from any stream.
+ */
+dcrf_status dcrf_lattice_build(const float *features, int64_t n, int d, dcrf_stream stream,
+                               dcrf_lattice *out);
+dcrf_status dcrf_lattice_build_batch(const float *features, const int64_t *offsets, int batch, int d,
+                                     dcrf_stream stream, dcrf_lattice *out);
+dcrf_status dcrf_lattice_destroy(dcrf_lattice lat);
+
+/* Sizes: n points, d features, m vertices, batch images (any output may be NULL). */
+dcrf_status dcrf_lattice_info(dcrf_lattice lat, int64_t *n, int *d, int64_t *m, int *batch);
+
+/* host [batch+1]: vertex range of each image. */
+dcrf_status dcrf_lattice_vertex_offsets(dcrf_lattice lat, int64_t *offsets);
+
+/* Reads and clears the device status word (synchronises the stream). */
+dcrf_status dcrf_lattice_status(dcrf_lattice lat, dcrf_stream stream);
+
+/*
+ * Copies the lattice structure into caller buffers (device; any may be NULL):
+ * keys [m][d] int32 (vertex coordinates 0..d-1; coordinate d is minus their
+ * sum), point_vertex [n][d+1] int32, point_weight [n][d+1] float32,
+ * neighbours [m][d+1][2] int32 (vertex id of v - w_j, v + w_j or -1).
+ */
+dcrf_status dcrf_lattice_export(dcrf_lattice lat, int32_t *keys, int32_t *point_vertex,
+                                float *point_weight, int32_t *neighbours, dcrf_stream stream);
+
+/*
+ * Eq. 6 through the lattice: out = K~ Y, K~ = s0 S^T B_d ... B_0 S, i.e.
+ * splat, d+1 axis blurs [1/4, 1/2, 1/4] (axis order 0..d), slice; not
+ * normalised (Appendix A).  Y, out: device [N][L] float32 (out may not alias
+ * Y), 1 <= L <= 64.  storage selects float32 or float16 lattice values.
+ */
+dcrf_status dcrf_filter(dcrf_lattice lat, const float *Y, int L, float *out, int storage,
+                        dcrf_stream stream);
+
+/* Adjoint K~^T U: the same chain with the blur axes in reverse order. */
+dcrf_status dcrf_filter_adjoint(dcrf_lattice lat, const float *U, int L, float *out, int storage,
+                                dcrf_stream stream);
+
+/*
+ * Frank-Wolfe on the convex QP relaxation S_cvx (Eq. 10; Algorithm 1 with the
+ * closed-form step and product reuse of Appendix B).
+ * unaries: device [N][L] phi.  lattices: host [n_kernels] handles over the
+ *   same points and batch; weights: host [n_kernels] w_m >= 0.
+ * compat: host [L][L] label compatibility mu, or NULL for Potts [i != j].
+ * Y: device [N][L]; on entry y^0 (rows on the simplex), on exit y^iters.
+ * records: host [iters][batch] or NULL; when given, the call synchronises.
+ * Pairwise operator: Psi = mu (x) (sum_m w_m K~_m - (sum_m w_m) I) (Eq. 7),
+ * d_a(i) = (sum_j |mu_ij|) max(0, (K~1)_a - sum_m w_m) (Eq. 11).
+ * One filter-equivalent per iteration; the step uses the exact derivative of
+ * the evaluated quadratic and is clipped to [0, 1].
+ */
+dcrf_status dcrf_qp_fw(const float *unaries, const dcrf_lattice *lattices, const float *weights,
+                       int n_kernels, const float *compat, int L, int iters, float *Y,
+                       dcrf_fw_record *records, int storage, dcrf_stream stream);
+
+/*
+ * CCCP on the generic DC relaxation (Section 5.1, Algorithm 2): outer steps
+ * linearise q(y) = y^T D y at y^t and run `inner` Frank-Wolfe iterations on
+ * phi^T y + y^T (Psi + D) y - 2 (d o y^t)^T y, warm-started at y^t.
+ * qp_energy: host [outer+1][batch] or NULL: S_QP(y) = phi^T y + y^T Psi y
+ * (Eq. 8) at the start and after every outer step (synchronises).
+ */
+dcrf_status dcrf_dc_cccp(const float *unaries, const dcrf_lattice *lattices, const float *weights,
+                         int n_kernels, const float *compat, int L, int outer, int inner, float *Y,
+                         double *qp_energy, int storage, dcrf_stream stream);
+
+/*
+ * LP relaxation subgradient (Eq. 18-20, Appendix D-E), Potts model.
+ * For every label i the pixels are sorted by descending y_a(i) (ties by
+ * ascending pixel index); the upper sums U_c = sum_{b after c} K~_cb come
+ * from the divide and conquer of Appendix E with power-of-two splits, where
+ * each sub-problem uses the lattice restricted to its own points; then
+ * G = phi + 2U - c with c_a = (K~1)_a - sum_m w_m.
+ * unaries, Y: device [N][L]; G: device [N][L] output.
+ * energy: host [batch] or NULL: S_LP(y) = <y, G> (synchronises).
+ */
+dcrf_status dcrf_lp_subgrad(const float *unaries, const float *Y, const dcrf_lattice *lattices,
+                            const float *weights, int n_kernels, int L, float *G, double *energy,
+                            dcrf_stream stream);
+
+/*
+ * Projected subgradient on the LP (Algorithm 3): y <- Proj_M(y - beta_t G),
+ * beta_t = beta0 / (1 + t).  beta0 <= 0 selects, per image,
+ * beta0 = 0.1 / max_{a,i} |G0_a(i) - mean_i G0_a(i)|.
+ * Y: device [N][L], in: y^0, out: the iterate with the lowest S_LP seen.
+ * energies: host [steps+1][batch] or NULL (synchronises).
+ */
+dcrf_status dcrf_lp_solve(const float *unaries, const dcrf_lattice *lattices, const float *weights,
+                          int n_kernels, int L, int steps, double beta0, float *Y, double *energies,
+                          dcrf_stream stream);
+
+/*
+ * Measurement hooks (no counterpart in the paper): when enabled, every
+ * kernel launch of the library is bracketed by CUDA events on its own stream
+ * and solvers launch without internal graphs.  dcrf_profile_read
+ * synchronises on the recorded events and fills up to `capacity` rows of
+ * (kernel name, launches, summed milliseconds); it returns the row count.
+ * names receive pointers to static strings.
+ */
+dcrf_status dcrf_profile_enable(int on);
+dcrf_status dcrf_profile_reset(void);
+int dcrf_profile_read(const char **names, int64_t *launches, double *ms, int capacity);
+
+/* Euclidean projection of every row of V [N][L] onto the simplex (device). */
+dcrf_status dcrf_simplex_project(const float *V, int64_t n, int L, float *Y, dcrf_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DCRF_H */

@@ -1,0 +1,143 @@
+// Shared definitions of the dense-CRF CUDA path (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+#include <vector>
+
+#include "dcrf.h"
+
+#define DCRF_MAX_D 8
+#define DCRF_MAX_L 64
+#define DCRF_MAX_KERNELS 4
+
+#define DCRF_TRY(expr)                                                     \
+    do {                                                                   \
+        cudaError_t e__ = (expr);                                          \
+        if (e__ != cudaSuccess) {                                          \
+            return e__ == cudaErrorMemoryAllocation ? DCRF_E_NOMEM : DCRF_E_CUDA; \
+        }                                                                  \
+    } while (0)
+
+#define DCRF_LAUNCHED()                                                    \
+    do {                                                                   \
+        cudaError_t e__ = cudaGetLastError();                              \
+        if (e__ != cudaSuccess) return DCRF_E_CUDA;                        \
+    } while (0)
+
+#define DCRF_CHECK_STATUS(expr)                                            \
+    do {                                                                   \
+        dcrf_status st__ = (expr);                                         \
+        if (st__ != DCRF_OK) return st__;                                  \
+    } while (0)
+
+// Empty hash slot.  Packed keys never reach it: every coordinate field is
+// kept below its all-ones value.
+#define DCRF_EMPTY_KEY 0xFFFFFFFFFFFFFFFFull
+
+struct dcrf_lattice_s {
+    int d = 0;
+    int64_t n = 0;
+    int64_t m = 0;
+    int batch = 0;
+    double s0 = 1.0;                 // output scale of the slice
+    std::vector<int64_t> point_off;  // host [batch+1]
+    std::vector<int64_t> vert_off;   // host [batch+1]
+    int64_t *point_off_d = nullptr;  // device [batch+1]
+    int64_t *vert_off_d = nullptr;   // device [batch+1]
+    int32_t *pvid = nullptr;         // [n][d+1] vertex of each simplex corner
+    float *pbary = nullptr;          // [n][d+1] barycentric weight of that corner
+    int32_t *keys = nullptr;         // [m][d]
+    int32_t *nbr = nullptr;          // [m][d+1][2]
+    int32_t *vimg = nullptr;         // [m] image of each vertex
+    float *ones = nullptr;           // [n] (K~_lattice 1)_a, s0 included
+    int *status = nullptr;           // device status word (first error wins)
+};
+
+// Records the first device-side error.
+__device__ __forceinline__ void dcrf_flag(int *status, int code) {
+    atomicCAS(status, 0, code);
+}
+
+__device__ __forceinline__ uint64_t dcrf_hash64(uint64_t k) {
+    // splitmix64 finaliser
+    k ^= k >> 30;
+    k *= 0xbf58476d1ce4e5b9ull;
+    k ^= k >> 27;
+    k *= 0x94d049bb133111ebull;
+    k ^= k >> 31;
+    return k;
+}
+
+__host__ __device__ __forceinline__ int dcrf_key_bits(int d) {
+    int b = 64 / d;
+    return b > 32 ? 32 : b;
+}
+
+// Work chunk: a contiguous range of rows inside one image.
+struct Chunk {
+    int64_t begin;
+    int32_t count;
+    int32_t image;
+};
+
+// Splits each image's row range into chunks of at most `size` rows.
+std::vector<Chunk> make_chunks(const std::vector<int64_t> &off, int size);
+
+// Host helpers (lattice.cu).
+dcrf_status dcrf_check_lattices(const dcrf_lattice *lats, int n_k);
+int dcrf_round4(int L);
+
+template <typename T>
+dcrf_status dcrf_alloc(T **p, size_t count, cudaStream_t s) {
+    *p = nullptr;
+    if (count == 0) return DCRF_OK;
+    cudaError_t e = cudaMallocAsync((void **)p, count * sizeof(T), s);
+    if (e != cudaSuccess) { *p = nullptr; return DCRF_E_NOMEM; }
+    return DCRF_OK;
+}
+
+// Stream-ordered scratch owned by one call; freed on the same stream.
+struct Scratch {
+    cudaStream_t s;
+    std::vector<void *> ptrs;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    template <typename T>
+    dcrf_status get(T **p, size_t count) {
+        dcrf_status st = dcrf_alloc(p, count, s);
+        if (st == DCRF_OK && *p) ptrs.push_back((void *)*p);
+        return st;
+    }
+    ~Scratch() {
+        for (void *p : ptrs) cudaFreeAsync(p, s);
+    }
+};
+
+dcrf_status dcrf_fill(float *p, float v, int64_t n, cudaStream_t s);
+
+// Per-kernel event timing (profile.cu); ids index the name table there.
+enum ProfId {
+    P_EMBED = 0, P_FINALIZE, P_NEIGHBOURS, P_SPLAT_DENSE, P_BLUR, P_SLICE,
+    P_FW_PIXEL, P_FW_LATDOT, P_FW_ALPHA, P_FW_LATUPD, P_FW_LIN,
+    P_LP_SORT, P_LP_RUNS, P_LP_SPLAT, P_LP_NEIGHBOURS, P_LP_BLUR, P_LP_SLICE, P_LP_COMBINE,
+    P_LP_PROJECT, P_LP_LOCAL
+};
+struct ProfScope {
+    ProfScope(int id, cudaStream_t s);
+    ~ProfScope();
+    int id_;
+    cudaStream_t s_;
+    void *a_;
+};
+bool dcrf_profiling();
+
+// Filter pipeline pieces shared by the solvers (lattice.cu).
+// Splat Y [n][L] (float32 rows) into V [m][Lp] float32 (V must be zeroed).
+dcrf_status dcrf_splat_dense(const dcrf_lattice lat, const float *Y, int L, float *V, int Lp,
+                             cudaStream_t s);
+// The d+1 blur passes (axis order 0..d, or d..0 when reverse).  src is
+// float32 [m][Lp]; the result lands in dst (float or half per storage); tmp is
+// scratch of the same type as dst.  src is left intact.
+dcrf_status dcrf_blur(const dcrf_lattice lat, const float *src, void *dst, void *tmp, int Lp,
+                      int storage, bool reverse, cudaStream_t s);

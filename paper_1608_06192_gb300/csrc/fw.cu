@@ -1,0 +1,756 @@
+// Frank-Wolfe on the convex QP relaxation and CCCP on the generic DC relaxation.
+//
+// Algorithm 1 with the closed-form step and the product reuse of Appendix B,
+// and Algorithm 2 (Section 5.1).  The operator is Psi + D with
+// Psi = mu (x) (K~ - sum_w I) (Eq. 7) and d_a(i) = sum_j |mu_ij| c_a (Eq. 11),
+// K~ = sum_m w_m s0_m S_m^T B_m S_m (one permutohedral lattice per kernel).
+//
+// Product reuse is done on the lattice instead of the pixels: since
+// y^{t+1} = y^t + alpha (s - y^t) and splat/blur are linear, the solver keeps
+//   Ylat = S y   and   BY = B S y          (per lattice, [M][Lp] float32)
+// and updates them with the same convex combination, so (Psi + D) y^{t+1} is
+// one slice of (1 - alpha) BY + alpha BS per pixel.  The one filter of every
+// iteration is the splat and blur of the one-hot s; the line-search terms
+// <y, P_s> and <s, P_s> use S^T = slice: <u, K~ v> = sum_m w_m s0_m <S u, B S v>
+// is a dot product over lattice vertices.  Each iteration therefore reads the
+// per-pixel state (y, phi - d, s, simplex table) once and writes y and s once.
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int kPixBlock = 128;   // pixels per block (one chunk)
+constexpr int kVertBlock = 128;  // vertices per block
+constexpr int NS = 8;            // per-pixel scalar sums, see k_fw_pixel
+
+struct FwLat {
+    const int32_t *pvid;
+    const float *pbary;
+    const int32_t *vimg;
+    int64_t m;
+    int d1;
+    float ws0;       // w_m * s0_m
+    float *Ylat;     // [m][Lp] S y
+    float *BY;       // [m][Lp] B S y (float32 master)
+    __half *BYh;     // [m][Lp] half copy of BY sliced by the pixel kernel (half storage only)
+    float *Slat;     // [m][Lp] S s
+    void *BS;        // [m][Lp] B S s (float or half)
+    void *tmp;       // blur scratch (same type as BS)
+};
+
+struct FwLats {
+    FwLat l[DCRF_MAX_KERNELS];
+    int nk;
+};
+
+__device__ __forceinline__ float4 ld4(const float *p, int64_t i) { return reinterpret_cast<const float4 *>(p)[i]; }
+__device__ __forceinline__ float4 ld4(const __half *p, int64_t i) {
+    uint2 raw = reinterpret_cast<const uint2 *>(p)[i];
+    float2 a = __half22float2(*reinterpret_cast<__half2 *>(&raw.x));
+    float2 b = __half22float2(*reinterpret_cast<__half2 *>(&raw.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void st4(float *p, int64_t i, float4 v) { reinterpret_cast<float4 *>(p)[i] = v; }
+__device__ __forceinline__ void st4h(__half *p, int64_t i, float4 v) {
+    __half2 lo = __floats2half2_rn(v.x, v.y), hi = __floats2half2_rn(v.z, v.w);
+    uint2 raw;
+    raw.x = *reinterpret_cast<uint32_t *>(&lo);
+    raw.y = *reinterpret_cast<uint32_t *>(&hi);
+    reinterpret_cast<uint2 *>(p)[i] = raw;
+}
+
+template <int N>
+__device__ __forceinline__ void block_reduce_add(double (&v)[N], double *acc) {
+    __shared__ double red[32][N];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        double x = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) red[warp][q] = x;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            double x = lane < nw ? red[lane][q] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if (lane == 0) atomicAdd(acc + q, x);
+        }
+    }
+}
+
+// Pixel phase of one iteration (or the start, alpha == 0).  It runs after the
+// lattice update, so BY already holds B S y' for y' = y + alpha (s - y):
+//   y'   = y + alpha (onehot(s) - y)
+//   Ky'  = sum_m w_m s0_m sum_k b_k BY_m[v_k]
+//   P    = mu (Ky' - sum_w y') + d o y'         = (Psi + D) y'
+//   g    = lin + 2 P,  s' = argmin_i g_i (lowest index on ties)
+// Sums per image (FP64), at y' and s':
+//   0: <lin, y'>   1: <y', P>   2: lin(s')   3: P(s')
+//   4: -sum_w <y', mu e_s'> + y'(s') d(s')   (pixel part of <y', (Psi+D) s'>)
+//   5: -sum_w mu(s', s') + d(s')            (pixel part of <s', (Psi+D) s'>)
+//   6: <y', D y'>  7: <phi, y'> (only when phi is given)
+// and S s' is splatted into Slat (warp-aggregated: lanes that hit the same
+// (vertex, label) add their weights in 2^-24 fixed point, one atomic per group).
+struct PixArgs {
+    const Chunk *chunks;
+    const double *alpha;   // [batch] or null (start: alpha = 0)
+    float *Y;              // [n][L]
+    const float *lin;      // [n][L] linear term (phi - d, or the CCCP one)
+    const float *phi;      // [n][L] or null
+    uint8_t *s;            // [n]
+    const float *c;        // [n] c_a >= 0
+    const float *mu;       // [L][L] (general mu only)
+    const float *musum;    // [L]
+    float sumw;
+    int L;
+    int Ls;                // shared-memory row stride (odd)
+    double *acc;           // [batch][NS]
+    int *status;
+};
+
+template <typename TB>
+__device__ __forceinline__ const TB *slice_src(const FwLat &lt);
+template <>
+__device__ __forceinline__ const float *slice_src<float>(const FwLat &lt) { return lt.BY; }
+template <>
+__device__ __forceinline__ const __half *slice_src<__half>(const FwLat &lt) { return lt.BYh; }
+
+template <int LP, typename TB, bool POTTS>
+__global__ void __launch_bounds__(kPixBlock) k_fw_pixel(PixArgs A, FwLats F) {
+    extern __shared__ float smem[];
+    float *sy = smem;
+    float *sl = smem + kPixBlock * A.Ls;
+    const Chunk ch = A.chunks[blockIdx.x];
+    const int L = A.L;
+    const int64_t base = ch.begin * (int64_t)L;
+    const int cnt = ch.count * L;
+    for (int i = threadIdx.x; i < cnt; i += kPixBlock) {
+        int r = i / L, c = i - r * L;
+        sy[r * A.Ls + c] = A.Y[base + i];
+        sl[r * A.Ls + c] = A.lin[base + i];
+    }
+    __syncthreads();
+    const bool start = A.alpha == nullptr;
+    const float al = start ? 0.f : (float)A.alpha[ch.image];
+    double part[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) part[q] = 0.0;
+    const int t = threadIdx.x;
+    const bool valid = t < ch.count;
+    const int64_t a = ch.begin + (valid ? t : 0);
+    int sb = 0;
+    if (valid) {
+        float y[LP], ky[LP];
+        const int sold = A.s[a];
+#pragma unroll
+        for (int i = 0; i < LP; ++i) {
+            float v = i < L ? sy[t * A.Ls + i] : 0.f;
+            if (!start && i < L) v = v + al * ((i == sold ? 1.f : 0.f) - v);
+            y[i] = v;
+            ky[i] = 0.f;
+        }
+#pragma unroll
+        for (int mm = 0; mm < DCRF_MAX_KERNELS; ++mm) {
+            if (mm >= F.nk) break;
+            const FwLat &lt = F.l[mm];
+            const TB *src = slice_src<TB>(lt);
+            for (int k = 0; k < lt.d1; ++k) {
+                const int v = __ldg(lt.pvid + a * lt.d1 + k);
+                if (v < 0) continue;
+                const float w = __ldg(lt.pbary + a * lt.d1 + k) * lt.ws0;
+#pragma unroll
+                for (int g = 0; g < LP / 4; ++g) {
+                    const float4 by = ld4(src, (int64_t)v * (LP / 4) + g);
+                    ky[4 * g + 0] += w * by.x;
+                    ky[4 * g + 1] += w * by.y;
+                    ky[4 * g + 2] += w * by.z;
+                    ky[4 * g + 3] += w * by.w;
+                }
+            }
+        }
+        const float ca = A.c[a];
+        // X = K~ y' - sum_w y' (in ky);  P = mu X + d o y'
+        float tot = 0.f;
+#pragma unroll
+        for (int i = 0; i < LP; ++i) {
+            ky[i] = i < L ? ky[i] - A.sumw * y[i] : 0.f;
+            tot += ky[i];
+        }
+        if (POTTS) {
+            const float dpot = (float)(L - 1) * ca;
+#pragma unroll
+            for (int i = 0; i < LP; ++i) ky[i] = i < L ? (tot - ky[i]) + dpot * y[i] : 0.f;
+        } else {
+            float X[LP];
+#pragma unroll
+            for (int i = 0; i < LP; ++i) X[i] = ky[i];
+#pragma unroll
+            for (int i = 0; i < LP; ++i) {
+                if (i < L) {
+                    float acc = 0.f;
+#pragma unroll
+                    for (int j = 0; j < LP; ++j)
+                        if (j < L) acc += A.mu[i * L + j] * X[j];
+                    ky[i] = acc + A.musum[i] * ca * y[i];
+                }
+            }
+        }
+        // ky now holds P = (Psi + D) y'
+        float best = INFINITY;
+        float s0 = 0.f, s1 = 0.f, s6 = 0.f, sy_ = 0.f;
+        float lin_s = 0.f, P_s = 0.f, y_s = 0.f;
+#pragma unroll
+        for (int i = 0; i < LP; ++i) {
+            if (i < L) {
+                const float li = sl[t * A.Ls + i];
+                const float g = li + 2.f * ky[i];
+                if (g < best) { best = g; sb = i; lin_s = li; P_s = ky[i]; y_s = y[i]; }
+                s0 += li * y[i];
+                s1 += y[i] * ky[i];
+                s6 += (POTTS ? (float)(L - 1) : A.musum[i]) * ca * y[i] * y[i];
+                sy_ += y[i];
+            }
+        }
+        if (!(best < INFINITY)) dcrf_flag(A.status, DCRF_E_NONFINITE);
+        float ymu;   // <y', mu e_s'> = sum_i y'_i mu(i, s')
+        float mu_ss;
+        if (POTTS) {
+            ymu = sy_ - y_s;
+            mu_ss = 0.f;
+        } else {
+            ymu = 0.f;
+#pragma unroll
+            for (int i = 0; i < LP; ++i)
+                if (i < L) ymu += y[i] * A.mu[i * L + sb];
+            mu_ss = A.mu[sb * L + sb];
+        }
+        const float ds = (POTTS ? (float)(L - 1) : A.musum[sb]) * ca;
+        part[0] = s0;
+        part[1] = s1;
+        part[2] = lin_s;
+        part[3] = P_s;
+        part[4] = (double)(-A.sumw * ymu) + (double)y_s * ds;
+        part[5] = (double)(-A.sumw * mu_ss) + ds;
+        part[6] = s6;
+        if (A.phi) {
+            float sp = 0.f;
+#pragma unroll
+            for (int i = 0; i < LP; ++i)
+                if (i < L) sp += A.phi[a * L + i] * y[i];
+            part[7] = sp;
+        }
+        if (!start) {
+#pragma unroll
+            for (int i = 0; i < LP; ++i)
+                if (i < L) sy[t * A.Ls + i] = y[i];
+        }
+        A.s[a] = (uint8_t)sb;
+    }
+    // splat of the one-hot s' (every lane of the block takes part)
+#pragma unroll
+    for (int mm = 0; mm < DCRF_MAX_KERNELS; ++mm) {
+        if (mm >= F.nk) break;
+        const FwLat &lt = F.l[mm];
+        for (int k = 0; k < lt.d1; ++k) {
+            long long key = -1;
+            unsigned u = 0;
+            if (valid) {
+                const int v = __ldg(lt.pvid + a * lt.d1 + k);
+                if (v >= 0) {
+                    key = (long long)v * LP + sb;
+                    u = __float2uint_rn(__ldg(lt.pbary + a * lt.d1 + k) * 16777216.f);
+                }
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, key);
+            const unsigned sum = __reduce_add_sync(peers, u);
+            if (key >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1)
+                atomicAdd(lt.Slat + key, (float)sum * (1.f / 16777216.f));
+        }
+    }
+    __syncthreads();
+    if (!start) {
+        for (int i = threadIdx.x; i < cnt; i += kPixBlock) {
+            int r = i / L, c = i - r * L;
+            A.Y[base + i] = sy[r * A.Ls + c];
+        }
+    }
+    block_reduce_add<NS>(part, A.acc + (int64_t)ch.image * NS);
+}
+
+// Lattice dot products for the line search:
+//   lacc[0] += w s0 sum_v sum_ij mu_ij Ylat[v][i] BS[v][j]   (= <y, K~-part of Psi s>)
+//   lacc[1] += w s0 sum_v sum_ij mu_ij Slat[v][i] BS[v][j]   (= <s, K~-part of Psi s>)
+struct DotArgs {
+    const Chunk *chunks;    // vertex chunks of lattice `which`
+    const float *mu;
+    int L;
+    int which;
+    double *lacc;           // [batch][2]
+};
+
+template <int LP, typename T, bool POTTS>
+__global__ void __launch_bounds__(kVertBlock) k_fw_latdot(DotArgs A, FwLat lt) {
+    const Chunk ch = A.chunks[blockIdx.x];
+    double part[2] = {0.0, 0.0};
+    if ((int)threadIdx.x < ch.count) {
+        const int64_t v = ch.begin + threadIdx.x;
+        float yv[LP], sv[LP], bv[LP];
+#pragma unroll
+        for (int g = 0; g < LP / 4; ++g) {
+            float4 a = ld4(lt.Ylat, v * (LP / 4) + g);
+            float4 b = ld4(lt.Slat, v * (LP / 4) + g);
+            float4 c = ld4((const T *)lt.BS, v * (LP / 4) + g);
+            yv[4 * g] = a.x; yv[4 * g + 1] = a.y; yv[4 * g + 2] = a.z; yv[4 * g + 3] = a.w;
+            sv[4 * g] = b.x; sv[4 * g + 1] = b.y; sv[4 * g + 2] = b.z; sv[4 * g + 3] = b.w;
+            bv[4 * g] = c.x; bv[4 * g + 1] = c.y; bv[4 * g + 2] = c.z; bv[4 * g + 3] = c.w;
+        }
+        float py = 0.f, ps = 0.f;
+        if (POTTS) {
+            float ty = 0.f, ts = 0.f, tb = 0.f, dy = 0.f, dsv = 0.f;
+#pragma unroll
+            for (int i = 0; i < LP; ++i) {
+                ty += yv[i]; ts += sv[i]; tb += bv[i];
+                dy += yv[i] * bv[i]; dsv += sv[i] * bv[i];
+            }
+            py = ty * tb - dy;
+            ps = ts * tb - dsv;
+        } else {
+            for (int i = 0; i < A.L; ++i) {
+                float mb = 0.f;
+#pragma unroll
+                for (int j = 0; j < LP; ++j)
+                    if (j < A.L) mb += A.mu[i * A.L + j] * bv[j];
+                py += yv[i] * mb;
+                ps += sv[i] * mb;
+            }
+        }
+        part[0] = (double)lt.ws0 * py;
+        part[1] = (double)lt.ws0 * ps;
+    }
+    block_reduce_add<2>(part, A.lacc + (int64_t)ch.image * 2);
+}
+
+// Step size and record of one iteration, one thread per image.
+__global__ void k_fw_alpha(int batch, double *acc, double *lacc, double *alpha, dcrf_fw_record *rec,
+                           int *counter, int *status) {
+    const int t = *counter;
+    for (int b = threadIdx.x; b < batch; b += blockDim.x) {
+        const double *sg = acc + (int64_t)b * NS;
+        const double yPs = lacc[2 * b + 0] + sg[4];
+        const double sPs = lacc[2 * b + 1] + sg[5];
+        const double A = sPs - sg[3] - yPs + sg[1];
+        const double B = sg[2] - sg[0] + yPs - 2.0 * sg[1] + sg[3];
+        double al;
+        if (!isfinite(A) || !isfinite(B)) {
+            dcrf_flag(status, DCRF_E_NONFINITE);
+            al = 0.0;
+        } else if (A > 0.0) {
+            al = fmin(1.0, fmax(0.0, -B / (2.0 * A)));
+        } else {
+            al = (A + B < 0.0) ? 1.0 : 0.0;
+        }
+        alpha[b] = al;
+        if (rec) {
+            dcrf_fw_record r;
+            r.energy = sg[0] + sg[1];
+            r.gap = sg[0] + 2.0 * sg[1] - sg[2] - 2.0 * sg[3];
+            r.alpha = al;
+            r.A = A;
+            r.B = B;
+            rec[(int64_t)t * batch + b] = r;
+        }
+        for (int q = 0; q < NS; ++q) acc[(int64_t)b * NS + q] = 0.0;
+        lacc[2 * b] = 0.0;
+        lacc[2 * b + 1] = 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *counter = t + 1;
+}
+
+// Ylat += alpha (Slat - Ylat); BY += alpha (BS - BY) (and its half copy); Slat = 0.
+template <typename T>
+__global__ void k_fw_latupd(FwLat lt, int G, const double *alpha) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= lt.m * G) return;
+    const int64_t v = idx / G;
+    const float al = (float)alpha[lt.vimg[v]];
+    float4 y = ld4(lt.Ylat, idx), s = ld4(lt.Slat, idx), by = ld4(lt.BY, idx), bs = ld4((const T *)lt.BS, idx);
+    y.x += al * (s.x - y.x); y.y += al * (s.y - y.y); y.z += al * (s.z - y.z); y.w += al * (s.w - y.w);
+    by.x += al * (bs.x - by.x); by.y += al * (bs.y - by.y); by.z += al * (bs.z - by.z); by.w += al * (bs.w - by.w);
+    st4(lt.Ylat, idx, y);
+    st4(lt.BY, idx, by);
+    if (lt.BYh) st4h(lt.BYh, idx, by);
+    st4(lt.Slat, idx, make_float4(0.f, 0.f, 0.f, 0.f));
+}
+
+__global__ void k_fw_to_half(const float *__restrict__ src, __half *__restrict__ dst, int64_t count4) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < count4) st4h(dst, i, ld4(src, i));
+}
+
+// c_a = max(0, sum_m w_m (K~_m 1)_a - sum_w);  lin = phi - d  (or phi - 2 d o y)
+__global__ void k_fw_c(int64_t n, FwLats F, const float *const *ones, const float *w, int nk, float sumw,
+                       float *c) {
+    int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    float s = 0.f;
+    for (int m = 0; m < nk; ++m) s += w[m] * ones[m][a];
+    s -= sumw;
+    c[a] = s > 0.f ? s : 0.f;
+}
+
+__global__ void k_fw_lin(int64_t n, int L, const float *phi, const float *c, const float *musum,
+                         const float *Y, float scale, float *lin, int *status) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n * L) return;
+    const int64_t a = i / L;
+    const int l = (int)(i - a * L);
+    const float p = phi[i];
+    if (!isfinite(p)) dcrf_flag(status, DCRF_E_NONFINITE);
+    const float yv = Y ? Y[i] : 1.f;
+    lin[i] = p - scale * musum[l] * c[a] * yv;
+}
+
+__global__ void k_fw_qp_energy(int batch, const double *acc, double *out) {
+    for (int b = threadIdx.x; b < batch; b += blockDim.x) {
+        const double *sg = acc + (int64_t)b * NS;
+        out[b] = sg[7] + sg[1] - sg[6];   // phi^T y + y^T (Psi + D) y - y^T D y
+    }
+}
+
+inline unsigned nblocks(int64_t work, int threads) { return (unsigned)((work + threads - 1) / threads); }
+
+// ---------------------------------------------------------------------------
+
+struct Solver {
+    cudaStream_t s;
+    Scratch sc;
+    int L = 0, Lp = 0, Ls = 0, batch = 0, storage = 0, nk = 0;
+    int64_t n = 0;
+    bool potts = true;
+    float sumw = 0.f;
+    const dcrf_lattice *lats = nullptr;
+    FwLats F{};
+    Chunk *pix_chunks = nullptr;
+    int n_pix_chunks = 0;
+    std::vector<Chunk *> vchunks;
+    std::vector<int> n_vchunks;
+    float *mu = nullptr, *musum = nullptr, *c = nullptr, *lin = nullptr;
+    uint8_t *sidx = nullptr;
+    double *acc = nullptr, *lacc = nullptr, *alpha = nullptr;
+    int *counter = nullptr;
+    dcrf_fw_record *rec = nullptr;
+    int *status = nullptr;
+
+    explicit Solver(cudaStream_t st) : s(st), sc(st) {}
+
+    dcrf_status setup(const float *unaries, const dcrf_lattice *lattices, const float *weights, int n_k,
+                      const float *compat, int L_, int store, float *Y, int max_records) {
+        DCRF_CHECK_STATUS(dcrf_check_lattices(lattices, n_k));
+        if (!unaries || !weights || !Y || L_ < 1 || L_ > DCRF_MAX_L) return DCRF_E_INVAL;
+        if (store != DCRF_STORAGE_F32 && store != DCRF_STORAGE_F16) return DCRF_E_INVAL;
+        if (L_ > 255) return DCRF_E_INVAL;
+        lats = lattices;
+        nk = n_k;
+        L = L_;
+        Lp = L <= 8 ? 8 : (L <= 24 ? 24 : 64);
+        Ls = L | 1;
+        storage = store;
+        n = lattices[0]->n;
+        batch = lattices[0]->batch;
+        status = lattices[0]->status;
+        sumw = 0.f;
+        for (int m = 0; m < nk; ++m) {
+            if (!(weights[m] >= 0.f)) return DCRF_E_INVAL;
+            sumw += weights[m];
+        }
+        // label compatibility
+        std::vector<float> mu_h(L * L), ms_h(L);
+        potts = compat == nullptr;
+        for (int i = 0; i < L; ++i) {
+            float acc_ = 0.f;
+            for (int j = 0; j < L; ++j) {
+                float v = compat ? compat[i * L + j] : (i == j ? 0.f : 1.f);
+                if (!std::isfinite(v)) return DCRF_E_INVAL;
+                mu_h[i * L + j] = v;
+                acc_ += std::fabs(v);
+            }
+            ms_h[i] = acc_;
+        }
+        const size_t esz = storage == DCRF_STORAGE_F16 ? 2 : 4;
+        DCRF_CHECK_STATUS(sc.get(&mu, (size_t)L * L));
+        DCRF_CHECK_STATUS(sc.get(&musum, (size_t)L));
+        DCRF_TRY(cudaMemcpyAsync(mu, mu_h.data(), L * L * sizeof(float), cudaMemcpyHostToDevice, s));
+        DCRF_TRY(cudaMemcpyAsync(musum, ms_h.data(), L * sizeof(float), cudaMemcpyHostToDevice, s));
+        // lattice workspaces
+        F.nk = nk;
+        for (int m = 0; m < nk; ++m) {
+            FwLat &l = F.l[m];
+            const dcrf_lattice lat = lattices[m];
+            l.pvid = lat->pvid;
+            l.pbary = lat->pbary;
+            l.vimg = lat->vimg;
+            l.m = lat->m;
+            l.d1 = lat->d + 1;
+            l.ws0 = (float)(weights[m] * lat->s0);
+            const size_t cnt = (size_t)(lat->m > 0 ? lat->m : 1) * Lp;
+            DCRF_CHECK_STATUS(sc.get(&l.Ylat, cnt));
+            DCRF_CHECK_STATUS(sc.get(&l.BY, cnt));
+            DCRF_CHECK_STATUS(sc.get(&l.Slat, cnt));
+            l.BYh = nullptr;
+            if (storage == DCRF_STORAGE_F16) DCRF_CHECK_STATUS(sc.get(&l.BYh, cnt));
+            char *bs, *tmp;
+            DCRF_CHECK_STATUS(sc.get(&bs, cnt * esz));
+            DCRF_CHECK_STATUS(sc.get(&tmp, cnt * esz));
+            l.BS = bs;
+            l.tmp = tmp;
+            DCRF_TRY(cudaMemsetAsync(l.Ylat, 0, cnt * sizeof(float), s));
+            DCRF_TRY(cudaMemsetAsync(bs, 0, cnt * esz, s));
+            auto ch = make_chunks(lat->vert_off, kVertBlock);
+            Chunk *chd = nullptr;
+            DCRF_CHECK_STATUS(sc.get(&chd, ch.size() > 0 ? ch.size() : 1));
+            if (!ch.empty())
+                DCRF_TRY(cudaMemcpyAsync(chd, ch.data(), ch.size() * sizeof(Chunk), cudaMemcpyHostToDevice, s));
+            vchunks.push_back(chd);
+            n_vchunks.push_back((int)ch.size());
+        }
+        auto pc = make_chunks(lattices[0]->point_off, kPixBlock);
+        n_pix_chunks = (int)pc.size();
+        DCRF_CHECK_STATUS(sc.get(&pix_chunks, pc.size() > 0 ? pc.size() : 1));
+        if (!pc.empty())
+            DCRF_TRY(cudaMemcpyAsync(pix_chunks, pc.data(), pc.size() * sizeof(Chunk), cudaMemcpyHostToDevice, s));
+        DCRF_CHECK_STATUS(sc.get(&c, (size_t)(n > 0 ? n : 1)));
+        DCRF_CHECK_STATUS(sc.get(&lin, (size_t)(n > 0 ? n : 1) * L));
+        DCRF_CHECK_STATUS(sc.get(&sidx, (size_t)(n > 0 ? n : 1)));
+        DCRF_CHECK_STATUS(sc.get(&acc, (size_t)batch * NS));
+        DCRF_CHECK_STATUS(sc.get(&lacc, (size_t)batch * 2));
+        DCRF_CHECK_STATUS(sc.get(&alpha, (size_t)batch));
+        DCRF_CHECK_STATUS(sc.get(&counter, 1));
+        DCRF_CHECK_STATUS(sc.get(&rec, (size_t)batch * (max_records > 0 ? max_records : 1)));
+        DCRF_TRY(cudaMemsetAsync(acc, 0, batch * NS * sizeof(double), s));
+        DCRF_TRY(cudaMemsetAsync(lacc, 0, batch * 2 * sizeof(double), s));
+        DCRF_TRY(cudaMemsetAsync(counter, 0, sizeof(int), s));
+        // c_a and lin = phi - d
+        const float *ones_h[DCRF_MAX_KERNELS];
+        for (int m = 0; m < nk; ++m) ones_h[m] = lattices[m]->ones;
+        const float **ones_d;
+        float *w_d;
+        DCRF_CHECK_STATUS(sc.get(&ones_d, nk));
+        DCRF_CHECK_STATUS(sc.get(&w_d, nk));
+        DCRF_TRY(cudaMemcpyAsync(ones_d, ones_h, nk * sizeof(float *), cudaMemcpyHostToDevice, s));
+        DCRF_TRY(cudaMemcpyAsync(w_d, weights, nk * sizeof(float), cudaMemcpyHostToDevice, s));
+        if (n > 0) {
+            k_fw_c<<<nblocks(n, 256), 256, 0, s>>>(n, F, ones_d, w_d, nk, sumw, c);
+            DCRF_LAUNCHED();
+            k_fw_lin<<<nblocks(n * L, 256), 256, 0, s>>>(n, L, unaries, c, musum, nullptr, 1.f, lin, status);
+            DCRF_LAUNCHED();
+        }
+        // Ylat = S y0, BY = B S y0
+        for (int m = 0; m < nk; ++m) {
+            FwLat &l = F.l[m];
+            DCRF_CHECK_STATUS(dcrf_splat_dense(lattices[m], Y, L, l.Ylat, Lp, s));
+            DCRF_CHECK_STATUS(dcrf_blur(lattices[m], l.Ylat, l.BY, l.Slat, Lp, DCRF_STORAGE_F32, false, s));
+            const size_t cnt = (size_t)(l.m > 0 ? l.m : 1) * Lp;
+            DCRF_TRY(cudaMemsetAsync(l.Slat, 0, cnt * sizeof(float), s));   // served as blur scratch
+            if (l.BYh && l.m > 0) {
+                k_fw_to_half<<<nblocks(l.m * Lp / 4, 256), 256, 0, s>>>(l.BY, l.BYh, l.m * Lp / 4);
+                DCRF_LAUNCHED();
+            }
+        }
+        return DCRF_OK;
+    }
+
+    template <int LPc, typename T, bool POT>
+    dcrf_status pixel_t(float *Y, const float *phi, bool start) {
+        PixArgs A;
+        A.chunks = pix_chunks;
+        A.alpha = start ? nullptr : alpha;
+        A.Y = Y;
+        A.lin = lin;
+        A.phi = phi;
+        A.s = sidx;
+        A.c = c;
+        A.mu = mu;
+        A.musum = musum;
+        A.sumw = sumw;
+        A.L = L;
+        A.Ls = Ls;
+        A.acc = acc;
+        A.status = status;
+        const size_t shm = 2 * kPixBlock * Ls * sizeof(float);
+        auto kern = k_fw_pixel<LPc, T, POT>;
+        if (shm > 48 * 1024) DCRF_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        if (n_pix_chunks > 0) {
+            ProfScope ps(P_FW_PIXEL, s);
+            kern<<<n_pix_chunks, kPixBlock, shm, s>>>(A, F);
+            DCRF_LAUNCHED();
+        }
+        return DCRF_OK;
+    }
+
+    template <typename T, bool POT>
+    dcrf_status pixel_lp(float *Y, const float *phi, bool start) {
+        if (Lp == 8) return pixel_t<8, T, POT>(Y, phi, start);
+        if (Lp == 24) return pixel_t<24, T, POT>(Y, phi, start);
+        return pixel_t<64, T, POT>(Y, phi, start);
+    }
+
+    dcrf_status pixel(float *Y, const float *phi, bool start) {
+        if (storage == DCRF_STORAGE_F16)
+            return potts ? pixel_lp<__half, true>(Y, phi, start) : pixel_lp<__half, false>(Y, phi, start);
+        return potts ? pixel_lp<float, true>(Y, phi, start) : pixel_lp<float, false>(Y, phi, start);
+    }
+
+    template <int LPc, typename T, bool POT>
+    dcrf_status latdot_t(int which) {
+        DotArgs A;
+        A.chunks = vchunks[which];
+        A.mu = mu;
+        A.L = L;
+        A.which = which;
+        A.lacc = lacc;
+        if (n_vchunks[which] > 0) {
+            ProfScope ps(P_FW_LATDOT, s);
+            k_fw_latdot<LPc, T, POT><<<n_vchunks[which], kVertBlock, 0, s>>>(A, F.l[which]);
+            DCRF_LAUNCHED();
+        }
+        return DCRF_OK;
+    }
+
+    template <typename T, bool POT>
+    dcrf_status latdot_lp(int which) {
+        if (Lp == 8) return latdot_t<8, T, POT>(which);
+        if (Lp == 24) return latdot_t<24, T, POT>(which);
+        return latdot_t<64, T, POT>(which);
+    }
+
+    dcrf_status latdot(int which) {
+        if (storage == DCRF_STORAGE_F16)
+            return potts ? latdot_lp<__half, true>(which) : latdot_lp<__half, false>(which);
+        return potts ? latdot_lp<float, true>(which) : latdot_lp<float, false>(which);
+    }
+
+    // One Frank-Wolfe iteration, state at (y, s, Slat = S s, BY = B S y).
+    dcrf_status iterate(float *Y, const float *phi) {
+        for (int m = 0; m < nk; ++m)
+            DCRF_CHECK_STATUS(dcrf_blur(lats[m], F.l[m].Slat, F.l[m].BS, F.l[m].tmp, Lp, storage, false, s));
+        for (int m = 0; m < nk; ++m) DCRF_CHECK_STATUS(latdot(m));
+        {
+            ProfScope ps(P_FW_ALPHA, s);
+            k_fw_alpha<<<1, 256, 0, s>>>(batch, acc, lacc, alpha, rec, counter, status);
+        }
+        DCRF_LAUNCHED();
+        const int G = Lp / 4;
+        for (int m = 0; m < nk; ++m) {
+            if (F.l[m].m == 0) continue;
+            ProfScope ps(P_FW_LATUPD, s);
+            if (storage == DCRF_STORAGE_F16)
+                k_fw_latupd<__half><<<nblocks(F.l[m].m * G, 256), 256, 0, s>>>(F.l[m], G, alpha);
+            else
+                k_fw_latupd<float><<<nblocks(F.l[m].m * G, 256), 256, 0, s>>>(F.l[m], G, alpha);
+            DCRF_LAUNCHED();
+        }
+        return pixel(Y, phi, false);
+    }
+
+    // Runs `iters` iterations; uses a CUDA graph of two iterations when the
+    // stream allows capture.
+    dcrf_status run(float *Y, int iters, const float *phi_last) {
+        int done = 0;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        DCRF_TRY(cudaStreamIsCapturing(s, &cs));
+        const bool graph_ok = s != nullptr && cs == cudaStreamCaptureStatusNone && iters >= 6 && !dcrf_profiling();
+        if (graph_ok) {
+            cudaGraph_t g = nullptr;
+            DCRF_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            dcrf_status st = iterate(Y, nullptr);
+            if (st == DCRF_OK) st = iterate(Y, nullptr);
+            cudaError_t e = cudaStreamEndCapture(s, &g);
+            if (st != DCRF_OK) { if (g) cudaGraphDestroy(g); return st; }
+            if (e != cudaSuccess) return DCRF_E_CUDA;
+            cudaGraphExec_t ge = nullptr;
+            e = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return DCRF_E_CUDA;
+            const int pairs = (iters - 1) / 2;
+            for (int p = 0; p < pairs; ++p) {
+                e = cudaGraphLaunch(ge, s);
+                if (e != cudaSuccess) { cudaGraphExecDestroy(ge); return DCRF_E_CUDA; }
+            }
+            cudaGraphExecDestroy(ge);
+            done = 2 * pairs;
+        }
+        for (int t = done; t < iters; ++t) DCRF_CHECK_STATUS(iterate(Y, t == iters - 1 ? phi_last : nullptr));
+        return DCRF_OK;
+    }
+};
+
+}  // namespace
+
+extern "C" dcrf_status dcrf_qp_fw(const float *unaries, const dcrf_lattice *lattices, const float *weights,
+                                  int n_kernels, const float *compat, int L, int iters, float *Y,
+                                  dcrf_fw_record *records, int storage, dcrf_stream stream) {
+    if (iters < 0) return DCRF_E_INVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    Solver S(s);
+    DCRF_CHECK_STATUS(S.setup(unaries, lattices, weights, n_kernels, compat, L, storage, Y, iters));
+    if (S.n == 0) return DCRF_OK;
+    DCRF_CHECK_STATUS(S.pixel(Y, nullptr, true));
+    DCRF_CHECK_STATUS(S.run(Y, iters, nullptr));
+    if (records && iters > 0) {
+        DCRF_TRY(cudaMemcpyAsync(records, S.rec, (size_t)iters * S.batch * sizeof(dcrf_fw_record),
+                                 cudaMemcpyDeviceToHost, s));
+        int h = 0;
+        DCRF_TRY(cudaMemcpyAsync(&h, S.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        DCRF_TRY(cudaStreamSynchronize(s));
+        if (h != 0) return (dcrf_status)h;
+    }
+    return DCRF_OK;
+}
+
+extern "C" dcrf_status dcrf_dc_cccp(const float *unaries, const dcrf_lattice *lattices, const float *weights,
+                                    int n_kernels, const float *compat, int L, int outer, int inner, float *Y,
+                                    double *qp_energy, int storage, dcrf_stream stream) {
+    if (outer < 0 || inner < 0) return DCRF_E_INVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    Solver S(s);
+    DCRF_CHECK_STATUS(S.setup(unaries, lattices, weights, n_kernels, compat, L, storage, Y, outer * inner));
+    if (S.n == 0) return DCRF_OK;
+    double *qe;
+    DCRF_CHECK_STATUS(S.sc.get(&qe, (size_t)(outer + 1) * S.batch));
+    // S_QP at y^0
+    DCRF_CHECK_STATUS(S.pixel(Y, unaries, true));
+    k_fw_qp_energy<<<1, 256, 0, s>>>(S.batch, S.acc, qe);
+    DCRF_LAUNCHED();
+    const int G = S.Lp / 4;
+    (void)G;
+    for (int o = 0; o < outer; ++o) {
+        // linearise q at y^t: lin = phi - 2 d o y^t
+        k_fw_lin<<<nblocks(S.n * L, 256), 256, 0, s>>>(S.n, L, unaries, S.c, S.musum, Y, 2.f, S.lin, S.status);
+        DCRF_LAUNCHED();
+        for (int m = 0; m < S.nk; ++m)
+            DCRF_TRY(cudaMemsetAsync(S.F.l[m].Slat, 0,
+                                     (size_t)(S.F.l[m].m > 0 ? S.F.l[m].m : 1) * S.Lp * sizeof(float), s));
+        DCRF_TRY(cudaMemsetAsync(S.acc, 0, S.batch * NS * sizeof(double), s));
+        DCRF_CHECK_STATUS(S.pixel(Y, inner == 0 ? unaries : nullptr, true));
+        DCRF_CHECK_STATUS(S.run(Y, inner, unaries));
+        k_fw_qp_energy<<<1, 256, 0, s>>>(S.batch, S.acc, qe + (int64_t)(o + 1) * S.batch);
+        DCRF_LAUNCHED();
+    }
+    if (qp_energy) {
+        DCRF_TRY(cudaMemcpyAsync(qp_energy, qe, (size_t)(outer + 1) * S.batch * sizeof(double),
+                                 cudaMemcpyDeviceToHost, s));
+        int h = 0;
+        DCRF_TRY(cudaMemcpyAsync(&h, S.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        DCRF_TRY(cudaStreamSynchronize(s));
+        if (h != 0) return (dcrf_status)h;
+    }
+    return DCRF_OK;
+}

@@ -1,0 +1,739 @@
+// Permutohedral lattice: features, GPU hash-table build, filter and adjoint.
+//
+// The paper computes sum_b k(f_a, f_b) v_b with the permutohedral-lattice
+// filter it cites (Section 3 "Filter-based Method", Eq. 6; Appendix A), not
+// normalised.  Lattice conventions (scale, elevation, enclosing simplex,
+// blur, output scale) are the ones stated in include/dcrf.h and the design doc:
+//   c_j   = f_j * alpha / sqrt((j+1)(j+2)),  alpha = (d+1) sqrt(2/3)
+//   x     = Helmert elevation onto sum(x) = 0 (FP64, one rounding per op)
+//   m_i   = rint(x_i / (d+1)), rank correction, barycentric weights
+//   blur  = d+1 Jacobi passes [1/4, 1/2, 1/4] along w_j = (d+1) e_j - 1
+//   s0    = (2 pi)^{d/2} alpha^d / (d+1)^{d - 1/2}
+#include <cub/device/device_scan.cuh>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+// ---------------------------------------------------------------------------
+// host helpers
+
+extern "C" const char *dcrf_status_string(int status) {
+    switch (status) {
+    case DCRF_OK: return "ok";
+    case DCRF_E_INVAL: return "invalid argument";
+    case DCRF_E_NOMEM: return "device allocation failed";
+    case DCRF_E_CUDA: return "CUDA error";
+    case DCRF_E_TABLE_FULL: return "lattice hash table full";
+    case DCRF_E_KEY_RANGE: return "lattice coordinate outside the packed key range";
+    case DCRF_E_TIMEOUT: return "bounded device wait expired";
+    case DCRF_E_NONFINITE: return "non-finite value";
+    default: return "unknown status";
+    }
+}
+
+extern "C" int dcrf_version(void) { return 1; }
+
+std::vector<Chunk> make_chunks(const std::vector<int64_t> &off, int size) {
+    std::vector<Chunk> out;
+    for (size_t b = 0; b + 1 < off.size(); ++b) {
+        for (int64_t s = off[b]; s < off[b + 1]; s += size) {
+            int64_t e = s + size < off[b + 1] ? s + size : off[b + 1];
+            out.push_back(Chunk{s, (int32_t)(e - s), (int32_t)b});
+        }
+    }
+    return out;
+}
+
+int dcrf_round4(int L) { return (L + 3) & ~3; }
+
+dcrf_status dcrf_check_lattices(const dcrf_lattice *lats, int n_k) {
+    if (!lats || n_k < 1 || n_k > DCRF_MAX_KERNELS) return DCRF_E_INVAL;
+    for (int i = 0; i < n_k; ++i) {
+        if (!lats[i]) return DCRF_E_INVAL;
+        if (lats[i]->n != lats[0]->n || lats[i]->batch != lats[0]->batch) return DCRF_E_INVAL;
+        for (int b = 0; b <= lats[0]->batch; ++b)
+            if (lats[i]->point_off[b] != lats[0]->point_off[b]) return DCRF_E_INVAL;
+    }
+    return DCRF_OK;
+}
+
+static inline unsigned blocks_for(int64_t work, int threads) {
+    return (unsigned)((work + threads - 1) / threads);
+}
+
+// ---------------------------------------------------------------------------
+// a1: features (Appendix G): (x/ta, y/ta, r/tb, g/tb, b/tb) and (x, y)/tg.
+
+__global__ void k_features(const float *__restrict__ rgb, const int64_t *__restrict__ off,
+                           const int32_t *__restrict__ widths, int batch, int64_t n, float ta,
+                           float tb, float tg, float *__restrict__ fb, float *__restrict__ fs) {
+    int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    int lo = 0, hi = batch - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= a) lo = mid; else hi = mid - 1;
+    }
+    int64_t local = a - off[lo];
+    int w = widths[lo];
+    float x = (float)(local % w);
+    float y = (float)(local / w);
+    if (fb) {
+        fb[a * 5 + 0] = __fdiv_rn(x, ta);
+        fb[a * 5 + 1] = __fdiv_rn(y, ta);
+        fb[a * 5 + 2] = __fdiv_rn(rgb[a * 3 + 0], tb);
+        fb[a * 5 + 3] = __fdiv_rn(rgb[a * 3 + 1], tb);
+        fb[a * 5 + 4] = __fdiv_rn(rgb[a * 3 + 2], tb);
+    }
+    if (fs) {
+        fs[a * 2 + 0] = __fdiv_rn(x, tg);
+        fs[a * 2 + 1] = __fdiv_rn(y, tg);
+    }
+}
+
+extern "C" dcrf_status dcrf_features(const float *rgb, const int32_t *widths, const int32_t *heights,
+                                     int batch, float theta_alpha, float theta_beta,
+                                     float theta_gamma, float *f_bil, float *f_sp,
+                                     dcrf_stream stream) {
+    if (!rgb || !widths || !heights || batch < 1 || (!f_bil && !f_sp)) return DCRF_E_INVAL;
+    if (!(theta_alpha > 0.f) || !(theta_beta > 0.f) || !(theta_gamma > 0.f)) return DCRF_E_INVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int64_t> off(batch + 1, 0);
+    for (int b = 0; b < batch; ++b) {
+        if (widths[b] < 1 || heights[b] < 1) return DCRF_E_INVAL;
+        off[b + 1] = off[b] + (int64_t)widths[b] * heights[b];
+    }
+    Scratch sc(s);
+    int64_t *off_d;
+    int32_t *w_d;
+    DCRF_CHECK_STATUS(sc.get(&off_d, batch + 1));
+    DCRF_CHECK_STATUS(sc.get(&w_d, batch));
+    DCRF_TRY(cudaMemcpyAsync(off_d, off.data(), (batch + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    DCRF_TRY(cudaMemcpyAsync(w_d, widths, batch * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    int64_t n = off[batch];
+    k_features<<<blocks_for(n, 256), 256, 0, s>>>(rgb, off_d, w_d, batch, n, theta_alpha, theta_beta,
+                                                  theta_gamma, f_bil, f_sp);
+    DCRF_LAUNCHED();
+    return DCRF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// a2: lattice build
+
+struct EmbedParams {
+    double sig[DCRF_MAX_D];
+    int batch;
+};
+
+__device__ __forceinline__ int find_image(const int64_t *__restrict__ off, int batch, int64_t a) {
+    int lo = 0, hi = batch - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= a) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Packs coordinates 0..D-1 of a vertex; false when a field leaves its range.
+template <int D>
+__device__ __forceinline__ bool pack_key(const long long *coord, uint64_t &key) {
+    constexpr int bits = (64 / D) > 32 ? 32 : (64 / D);
+    const long long bias = 1ll << (bits - 1);
+    const long long top = (bits == 32) ? 0xFFFFFFFFll : ((1ll << bits) - 1);
+    key = 0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        long long f = coord[i] + bias;
+        if (f < 0 || f >= top) return false;
+        key |= (uint64_t)f << (bits * i);
+    }
+    return true;
+}
+
+template <int D>
+__global__ void k_embed_insert(const float *__restrict__ feat, int64_t n, EmbedParams P,
+                               const int64_t *__restrict__ point_off,
+                               const int64_t *__restrict__ tab_base,
+                               const int64_t *__restrict__ tab_mask,
+                               unsigned long long *__restrict__ table, int64_t *__restrict__ pslot,
+                               float *__restrict__ pbary, int *__restrict__ status) {
+    constexpr int D1 = D + 1;
+    int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    int img = find_image(point_off, P.batch, a);
+
+    // scale and elevate (one IEEE rounding per operation, no contraction)
+    double c[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) c[j] = __dmul_rn((double)feat[a * D + j], P.sig[j]);
+    double x[D1];
+    double sm = 0.0;
+#pragma unroll
+    for (int i = D; i >= 1; --i) {
+        x[i] = __dsub_rn(sm, __dmul_rn((double)i, c[i - 1]));
+        sm = __dadd_rn(sm, c[i - 1]);
+    }
+    x[0] = sm;
+
+    // nearest remainder-0 point
+    long long mi[D1];
+    double delta[D1];
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < D1; ++i) {
+        double q = rint(__ddiv_rn(x[i], (double)D1));
+        if (!(fabs(q) < 1.0e12)) ok = false;   // also catches NaN
+        mi[i] = ok ? (long long)q : 0;
+        delta[i] = __dsub_rn(x[i], __dmul_rn((double)D1, q));
+    }
+    if (!ok) {
+        dcrf_flag(status, DCRF_E_NONFINITE);
+#pragma unroll
+        for (int k = 0; k < D1; ++k) { pslot[a * D1 + k] = -1; pbary[a * D1 + k] = 0.f; }
+        return;
+    }
+    int rank[D1];
+#pragma unroll
+    for (int i = 0; i < D1; ++i) {
+        int r = 0;
+#pragma unroll
+        for (int j = 0; j < D1; ++j)
+            r += (delta[j] > delta[i]) || (delta[j] == delta[i] && j < i);
+        rank[i] = r;
+    }
+    long long s = 0;
+#pragma unroll
+    for (int i = 0; i < D1; ++i) s += mi[i];
+    if (s > 0) {
+#pragma unroll
+        for (int i = 0; i < D1; ++i) {
+            if (rank[i] >= D1 - s) { mi[i] -= 1; rank[i] -= (int)(D1 - s); }
+            else rank[i] += (int)s;
+        }
+    } else if (s < 0) {
+#pragma unroll
+        for (int i = 0; i < D1; ++i) {
+            if (rank[i] < -s) { mi[i] += 1; rank[i] += (int)(D1 + s); }
+            else rank[i] += (int)s;
+        }
+    }
+    double ys[D1];
+#pragma unroll
+    for (int p = 0; p < D1; ++p) ys[p] = 0.0;
+#pragma unroll
+    for (int i = 0; i < D1; ++i) {
+        double dl = __dsub_rn(x[i], __dmul_rn((double)D1, (double)mi[i]));
+#pragma unroll
+        for (int p = 0; p < D1; ++p)
+            if (rank[i] == p) ys[p] = dl;
+    }
+    double b[D1];
+#pragma unroll
+    for (int k = 1; k < D1; ++k) b[k] = __ddiv_rn(__dsub_rn(ys[D - k], ys[D + 1 - k]), (double)D1);
+    b[0] = __dsub_rn(1.0, __ddiv_rn(__dsub_rn(ys[0], ys[D]), (double)D1));
+
+    const int64_t base = tab_base[img];
+    const uint64_t mask = (uint64_t)tab_mask[img];
+#pragma unroll
+    for (int k = 0; k < D1; ++k) {
+        pbary[a * D1 + k] = (float)b[k];
+        long long coord[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) coord[i] = D1 * mi[i] + k - (rank[i] >= D1 - k ? D1 : 0);
+        uint64_t key;
+        int64_t found = -1;
+        if (!pack_key<D>(coord, key)) {
+            dcrf_flag(status, DCRF_E_KEY_RANGE);
+        } else {
+            uint64_t h = dcrf_hash64(key);
+            for (uint64_t probe = 0; probe <= mask; ++probe) {
+                int64_t slot = base + (int64_t)((h + probe) & mask);
+                unsigned long long cur = *((volatile unsigned long long *)&table[slot]);
+                if (cur == key) { found = slot; break; }
+                if (cur == DCRF_EMPTY_KEY) {
+                    unsigned long long prev = atomicCAS(&table[slot], DCRF_EMPTY_KEY, (unsigned long long)key);
+                    if (prev == DCRF_EMPTY_KEY || prev == key) { found = slot; break; }
+                }
+            }
+            if (found < 0) dcrf_flag(status, DCRF_E_TABLE_FULL);
+        }
+        pslot[a * D1 + k] = found;
+    }
+}
+
+__global__ void k_occupied(const unsigned long long *__restrict__ table, int64_t slots,
+                           int32_t *__restrict__ flag) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < slots) flag[i] = table[i] != DCRF_EMPTY_KEY ? 1 : 0;
+}
+
+template <int D>
+__global__ void k_finalize_slots(const unsigned long long *__restrict__ table, int64_t slots,
+                                 const int32_t *__restrict__ scan, const int64_t *__restrict__ tab_base,
+                                 int batch, int32_t *__restrict__ keys, int32_t *__restrict__ vimg) {
+    constexpr int bits = (64 / D) > 32 ? 32 : (64 / D);
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= slots) return;
+    uint64_t key = table[i];
+    if (key == DCRF_EMPTY_KEY) return;
+    int v = scan[i];
+    const long long bias = 1ll << (bits - 1);
+    const uint64_t fmask = (bits == 32) ? 0xFFFFFFFFull : ((1ull << bits) - 1);
+#pragma unroll
+    for (int c = 0; c < D; ++c) keys[(int64_t)v * D + c] = (int32_t)((long long)((key >> (bits * c)) & fmask) - bias);
+    vimg[v] = find_image(tab_base, batch, i);
+}
+
+__global__ void k_assign_vid(const int64_t *__restrict__ pslot, int64_t count,
+                             const int32_t *__restrict__ scan, int32_t *__restrict__ pvid) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < count) {
+        int64_t s = pslot[i];
+        pvid[i] = s >= 0 ? scan[s] : -1;
+    }
+}
+
+__global__ void k_vertex_offsets(const int32_t *__restrict__ scan, const int32_t *__restrict__ flag,
+                                 const int64_t *__restrict__ tab_base, int batch, int64_t slots,
+                                 int64_t *__restrict__ vert_off) {
+    for (int b = threadIdx.x; b < batch; b += blockDim.x) vert_off[b] = scan[tab_base[b]];
+    if (threadIdx.x == 0) vert_off[batch] = (int64_t)scan[slots - 1] + flag[slots - 1];
+}
+
+template <int D>
+__global__ void k_neighbours(const int32_t *__restrict__ keys, const int32_t *__restrict__ vimg, int64_t m,
+                             const unsigned long long *__restrict__ table, const int32_t *__restrict__ scan,
+                             const int64_t *__restrict__ tab_base, const int64_t *__restrict__ tab_mask,
+                             int32_t *__restrict__ nbr) {
+    constexpr int D1 = D + 1;
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= m) return;
+    long long k0[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) k0[i] = keys[v * D + i];
+    int img = vimg[v];
+    const int64_t base = tab_base[img];
+    const uint64_t mask = (uint64_t)tab_mask[img];
+    for (int j = 0; j < D1; ++j) {
+        for (int side = 0; side < 2; ++side) {
+            const long long sgn = side ? 1 : -1;
+            long long c[D];
+#pragma unroll
+            for (int i = 0; i < D; ++i) c[i] = k0[i] + sgn * (i == j ? (long long)D : -1ll);
+            int32_t found = -1;
+            uint64_t key;
+            if (pack_key<D>(c, key)) {
+                uint64_t h = dcrf_hash64(key);
+                for (uint64_t probe = 0; probe <= mask; ++probe) {
+                    int64_t slot = base + (int64_t)((h + probe) & mask);
+                    unsigned long long cur = table[slot];
+                    if (cur == key) { found = scan[slot]; break; }
+                    if (cur == DCRF_EMPTY_KEY) break;
+                }
+            }
+            nbr[(v * D1 + j) * 2 + side] = found;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// filter pieces
+
+__device__ __forceinline__ float4 load4(const float *p, int64_t i) { return reinterpret_cast<const float4 *>(p)[i]; }
+__device__ __forceinline__ float4 load4(const __half *p, int64_t i) {
+    uint2 raw = reinterpret_cast<const uint2 *>(p)[i];
+    __half2 lo = *reinterpret_cast<__half2 *>(&raw.x);
+    __half2 hi = *reinterpret_cast<__half2 *>(&raw.y);
+    float2 a = __half22float2(lo), b = __half22float2(hi);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void store4(float *p, int64_t i, float4 v) { reinterpret_cast<float4 *>(p)[i] = v; }
+__device__ __forceinline__ void store4(__half *p, int64_t i, float4 v) {
+    __half2 lo = __floats2half2_rn(v.x, v.y), hi = __floats2half2_rn(v.z, v.w);
+    uint2 raw;
+    raw.x = *reinterpret_cast<uint32_t *>(&lo);
+    raw.y = *reinterpret_cast<uint32_t *>(&hi);
+    reinterpret_cast<uint2 *>(p)[i] = raw;
+}
+
+// One Jacobi pass along axis j: out[v] = in[v]/2 + (in[v - w_j] + in[v + w_j])/4.
+template <typename Tin, typename Tout>
+__global__ void k_blur_pass(const Tin *__restrict__ in, Tout *__restrict__ out,
+                            const int32_t *__restrict__ nbr, int64_t m, int G, int j, int D1) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= m * G) return;
+    int64_t v = idx / G;
+    int g = (int)(idx - v * G);
+    int2 nb = reinterpret_cast<const int2 *>(nbr)[v * D1 + j];
+    float4 c = load4(in, idx);
+    float4 r = make_float4(0.5f * c.x, 0.5f * c.y, 0.5f * c.z, 0.5f * c.w);
+    if (nb.x >= 0) {
+        float4 q = load4(in, (int64_t)nb.x * G + g);
+        r.x += 0.25f * q.x; r.y += 0.25f * q.y; r.z += 0.25f * q.z; r.w += 0.25f * q.w;
+    }
+    if (nb.y >= 0) {
+        float4 q = load4(in, (int64_t)nb.y * G + g);
+        r.x += 0.25f * q.x; r.y += 0.25f * q.y; r.z += 0.25f * q.z; r.w += 0.25f * q.w;
+    }
+    store4(out, idx, r);
+}
+
+template <typename T>
+static dcrf_status blur_typed(const dcrf_lattice lat, const float *src, T *dst, T *tmp, int Lp,
+                              bool reverse, cudaStream_t s) {
+    const int D = lat->d, D1 = D + 1, G = Lp / 4;
+    const int64_t work = lat->m * G;
+    if (work == 0) return DCRF_OK;
+    const unsigned nb = blocks_for(work, 256);
+    for (int p = 0; p < D1; ++p) {
+        int j = reverse ? D - p : p;
+        T *out = ((D - p) % 2 == 0) ? dst : tmp;
+        ProfScope ps(P_BLUR, s);
+        if (p == 0) {
+            k_blur_pass<float, T><<<nb, 256, 0, s>>>(src, out, lat->nbr, lat->m, G, j, D1);
+        } else {
+            T *in = ((D - p + 1) % 2 == 0) ? dst : tmp;
+            k_blur_pass<T, T><<<nb, 256, 0, s>>>(in, out, lat->nbr, lat->m, G, j, D1);
+        }
+        DCRF_LAUNCHED();
+    }
+    return DCRF_OK;
+}
+
+dcrf_status dcrf_blur(const dcrf_lattice lat, const float *src, void *dst, void *tmp, int Lp,
+                      int storage, bool reverse, cudaStream_t s) {
+    if (storage == DCRF_STORAGE_F16)
+        return blur_typed<__half>(lat, src, (__half *)dst, (__half *)tmp, Lp, reverse, s);
+    return blur_typed<float>(lat, src, (float *)dst, (float *)tmp, Lp, reverse, s);
+}
+
+// Dense splat: V[vertex_k(a)][c] += b_k(a) * Y[a][c].
+__global__ void k_splat_dense(const float *__restrict__ Y, int64_t n, int L, int Lp, int D1,
+                              const int32_t *__restrict__ pvid, const float *__restrict__ pbary,
+                              float *__restrict__ V) {
+    int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    for (int k = 0; k < D1; ++k) {
+        int v = pvid[a * D1 + k];
+        if (v < 0) continue;
+        float w = pbary[a * D1 + k];
+        float *row = V + (int64_t)v * Lp;
+        for (int c = 0; c < L; ++c) atomicAdd(row + c, w * Y[a * L + c]);
+    }
+}
+
+dcrf_status dcrf_splat_dense(const dcrf_lattice lat, const float *Y, int L, float *V, int Lp,
+                             cudaStream_t s) {
+    if (lat->n == 0) return DCRF_OK;
+    ProfScope ps(P_SPLAT_DENSE, s);
+    k_splat_dense<<<blocks_for(lat->n, 128), 128, 0, s>>>(Y, lat->n, L, Lp, lat->d + 1, lat->pvid,
+                                                          lat->pbary, V);
+    DCRF_LAUNCHED();
+    return DCRF_OK;
+}
+
+// Slice: out[a][c] = s0 * sum_k b_k(a) V[vertex_k(a)][c].
+template <typename T>
+__global__ void k_slice(const T *__restrict__ V, int64_t n, int L, int G, int D1,
+                        const int32_t *__restrict__ pvid, const float *__restrict__ pbary, float s0,
+                        float *__restrict__ out) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * G) return;
+    int64_t a = idx / G;
+    int g = (int)(idx - a * G);
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = 0; k < D1; ++k) {
+        int v = pvid[a * D1 + k];
+        if (v < 0) continue;
+        float w = pbary[a * D1 + k];
+        float4 q = load4(V, (int64_t)v * G + g);
+        r.x += w * q.x; r.y += w * q.y; r.z += w * q.z; r.w += w * q.w;
+    }
+    float vals[4] = {r.x, r.y, r.z, r.w};
+    for (int i = 0; i < 4; ++i) {
+        int c = 4 * g + i;
+        if (c < L) out[a * L + c] = s0 * vals[i];
+    }
+}
+
+static dcrf_status filter_impl(const dcrf_lattice lat, const float *Y, int L, float *out, int storage,
+                               bool reverse, cudaStream_t s) {
+    if (!lat || !Y || !out || L < 1 || L > DCRF_MAX_L) return DCRF_E_INVAL;
+    if (storage != DCRF_STORAGE_F32 && storage != DCRF_STORAGE_F16) return DCRF_E_INVAL;
+    if (lat->n == 0) return DCRF_OK;
+    const int Lp = dcrf_round4(L);
+    const size_t esz = storage == DCRF_STORAGE_F16 ? 2 : 4;
+    Scratch sc(s);
+    float *V;
+    char *dst, *tmp;
+    DCRF_CHECK_STATUS(sc.get(&V, (size_t)lat->m * Lp));
+    DCRF_CHECK_STATUS(sc.get(&dst, (size_t)lat->m * Lp * esz));
+    DCRF_CHECK_STATUS(sc.get(&tmp, (size_t)lat->m * Lp * esz));
+    DCRF_TRY(cudaMemsetAsync(V, 0, (size_t)lat->m * Lp * sizeof(float), s));
+    DCRF_CHECK_STATUS(dcrf_splat_dense(lat, Y, L, V, Lp, s));
+    DCRF_CHECK_STATUS(dcrf_blur(lat, V, dst, tmp, Lp, storage, reverse, s));
+    const int G = Lp / 4;
+    const unsigned nb = blocks_for(lat->n * G, 256);
+    ProfScope ps(P_SLICE, s);
+    if (storage == DCRF_STORAGE_F16)
+        k_slice<__half><<<nb, 256, 0, s>>>((const __half *)dst, lat->n, L, G, lat->d + 1, lat->pvid, lat->pbary,
+                                           (float)lat->s0, out);
+    else
+        k_slice<float><<<nb, 256, 0, s>>>((const float *)dst, lat->n, L, G, lat->d + 1, lat->pvid, lat->pbary,
+                                          (float)lat->s0, out);
+    DCRF_LAUNCHED();
+    return DCRF_OK;
+}
+
+extern "C" dcrf_status dcrf_filter(dcrf_lattice lat, const float *Y, int L, float *out, int storage,
+                                   dcrf_stream stream) {
+    if (Y == out) return DCRF_E_INVAL;
+    return filter_impl(lat, Y, L, out, storage, false, (cudaStream_t)stream);
+}
+
+extern "C" dcrf_status dcrf_filter_adjoint(dcrf_lattice lat, const float *U, int L, float *out,
+                                           int storage, dcrf_stream stream) {
+    if (U == out) return DCRF_E_INVAL;
+    return filter_impl(lat, U, L, out, storage, true, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// build driver
+
+static void lattice_free(dcrf_lattice lat) {
+    if (!lat) return;
+    cudaFree(lat->point_off_d);
+    cudaFree(lat->vert_off_d);
+    cudaFree(lat->pvid);
+    cudaFree(lat->pbary);
+    cudaFree(lat->keys);
+    cudaFree(lat->nbr);
+    cudaFree(lat->vimg);
+    cudaFree(lat->ones);
+    cudaFree(lat->status);
+    delete lat;
+}
+
+__global__ void k_fill(float *p, float v, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+dcrf_status dcrf_fill(float *p, float v, int64_t n, cudaStream_t s) {
+    if (n <= 0) return DCRF_OK;
+    k_fill<<<blocks_for(n, 256), 256, 0, s>>>(p, v, n);
+    DCRF_LAUNCHED();
+    return DCRF_OK;
+}
+
+template <int D>
+static dcrf_status build_typed(dcrf_lattice lat, const float *feat, cudaStream_t s) {
+    constexpr int D1 = D + 1;
+    const int batch = lat->batch;
+    const int64_t n = lat->n;
+    // one power-of-two table segment per image, at least twice the largest
+    // possible vertex count n_b (d+1)
+    std::vector<int64_t> base(batch), mask(batch);
+    int64_t slots = 0;
+    for (int b = 0; b < batch; ++b) {
+        int64_t nb = lat->point_off[b + 1] - lat->point_off[b];
+        int64_t want = 2 * nb * D1 < 64 ? 64 : 2 * nb * D1;
+        int64_t cap = 64;
+        while (cap < want) cap <<= 1;
+        base[b] = slots;
+        mask[b] = cap - 1;
+        slots += cap;
+    }
+    if (slots >= (1ll << 31)) return DCRF_E_INVAL;   // vertex ids are int32
+
+    Scratch sc(s);
+    unsigned long long *table;
+    int64_t *pslot, *base_d, *mask_d;
+    int32_t *flag, *scan;
+    DCRF_CHECK_STATUS(sc.get(&table, slots));
+    DCRF_CHECK_STATUS(sc.get(&pslot, (size_t)n * D1 + 1));
+    DCRF_CHECK_STATUS(sc.get(&base_d, batch));
+    DCRF_CHECK_STATUS(sc.get(&mask_d, batch));
+    DCRF_CHECK_STATUS(sc.get(&flag, slots));
+    DCRF_CHECK_STATUS(sc.get(&scan, slots));
+    DCRF_TRY(cudaMemcpyAsync(base_d, base.data(), batch * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    DCRF_TRY(cudaMemcpyAsync(mask_d, mask.data(), batch * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    DCRF_TRY(cudaMemsetAsync(table, 0xFF, slots * sizeof(unsigned long long), s));
+
+    EmbedParams P;
+    const double alpha = (double)D1 * std::sqrt(2.0 / 3.0);
+    for (int j = 0; j < DCRF_MAX_D; ++j)
+        P.sig[j] = j < D ? alpha / std::sqrt((double)((j + 1) * (j + 2))) : 0.0;
+    P.batch = batch;
+    lat->s0 = std::pow(2.0 * M_PI, D / 2.0) * std::pow(alpha, (double)D) / std::pow((double)D1, D - 0.5);
+
+    if (n > 0) {
+        ProfScope ps(P_EMBED, s);
+        k_embed_insert<D><<<blocks_for(n, 128), 128, 0, s>>>(feat, n, P, lat->point_off_d, base_d, mask_d, table,
+                                                             pslot, lat->pbary, lat->status);
+        DCRF_LAUNCHED();
+    }
+    k_occupied<<<blocks_for(slots, 256), 256, 0, s>>>(table, slots, flag);
+    DCRF_LAUNCHED();
+    size_t tmp_bytes = 0;
+    DCRF_TRY(cub::DeviceScan::ExclusiveSum(nullptr, tmp_bytes, flag, scan, (int)slots, s));
+    void *tmp;
+    DCRF_CHECK_STATUS(sc.get((char **)&tmp, tmp_bytes));
+    DCRF_TRY(cub::DeviceScan::ExclusiveSum(tmp, tmp_bytes, flag, scan, (int)slots, s));
+    k_vertex_offsets<<<1, 1024, 0, s>>>(scan, flag, base_d, batch, slots, lat->vert_off_d);
+    DCRF_LAUNCHED();
+    lat->vert_off.assign(batch + 1, 0);
+    DCRF_TRY(cudaMemcpyAsync(lat->vert_off.data(), lat->vert_off_d, (batch + 1) * sizeof(int64_t),
+                             cudaMemcpyDeviceToHost, s));
+    int hstatus = 0;
+    DCRF_TRY(cudaMemcpyAsync(&hstatus, lat->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DCRF_TRY(cudaStreamSynchronize(s));
+    if (hstatus != 0) return (dcrf_status)hstatus;
+    lat->m = lat->vert_off[batch];
+    const int64_t m = lat->m;
+
+    DCRF_TRY(cudaMalloc(&lat->keys, (m > 0 ? m : 1) * D * sizeof(int32_t)));
+    DCRF_TRY(cudaMalloc(&lat->vimg, (m > 0 ? m : 1) * sizeof(int32_t)));
+    DCRF_TRY(cudaMalloc(&lat->nbr, (m > 0 ? m : 1) * D1 * 2 * sizeof(int32_t)));
+    k_finalize_slots<D><<<blocks_for(slots, 256), 256, 0, s>>>(table, slots, scan, base_d, batch, lat->keys,
+                                                               lat->vimg);
+    DCRF_LAUNCHED();
+    if (n > 0) {
+        k_assign_vid<<<blocks_for(n * D1, 256), 256, 0, s>>>(pslot, n * D1, scan, lat->pvid);
+        DCRF_LAUNCHED();
+    }
+    if (m > 0) {
+        k_neighbours<D><<<blocks_for(m, 128), 128, 0, s>>>(lat->keys, lat->vimg, m, table, scan, base_d, mask_d,
+                                                           lat->nbr);
+        DCRF_LAUNCHED();
+    }
+    // K~ 1 for the d vector of Eq. 11
+    if (n > 0) {
+        float *V, *A, *B;
+        DCRF_CHECK_STATUS(sc.get(&V, (size_t)m * 4));
+        DCRF_CHECK_STATUS(sc.get(&A, (size_t)m * 4));
+        DCRF_CHECK_STATUS(sc.get(&B, (size_t)m * 4));
+        float *ones_in;
+        DCRF_CHECK_STATUS(sc.get(&ones_in, (size_t)n));
+        DCRF_TRY(cudaMemsetAsync(V, 0, (size_t)m * 4 * sizeof(float), s));
+        // fill ones (float 1.0f bit pattern is not bytewise, use a kernel)
+        DCRF_CHECK_STATUS(dcrf_fill(ones_in, 1.0f, n, s));
+        DCRF_CHECK_STATUS(dcrf_splat_dense(lat, ones_in, 1, V, 4, s));
+        DCRF_CHECK_STATUS(dcrf_blur(lat, V, A, B, 4, DCRF_STORAGE_F32, false, s));
+        k_slice<float><<<blocks_for(n, 256), 256, 0, s>>>(A, n, 1, 1, D1, lat->pvid, lat->pbary, (float)lat->s0,
+                                                          lat->ones);
+        DCRF_LAUNCHED();
+    }
+    DCRF_TRY(cudaMemcpyAsync(&hstatus, lat->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DCRF_TRY(cudaStreamSynchronize(s));
+    if (hstatus != 0) return (dcrf_status)hstatus;
+    return DCRF_OK;
+}
+
+extern "C" dcrf_status dcrf_lattice_build_batch(const float *features, const int64_t *offsets, int batch,
+                                                int d, dcrf_stream stream, dcrf_lattice *out) {
+    if (!out) return DCRF_E_INVAL;
+    *out = nullptr;
+    if (!offsets || batch < 1 || d < 1 || d > DCRF_MAX_D) return DCRF_E_INVAL;
+    if (offsets[0] != 0) return DCRF_E_INVAL;
+    for (int b = 0; b < batch; ++b)
+        if (offsets[b + 1] < offsets[b]) return DCRF_E_INVAL;
+    const int64_t n = offsets[batch];
+    if (n > 0 && !features) return DCRF_E_INVAL;
+    if (n >= (1ll << 31) / (d + 1)) return DCRF_E_INVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    dcrf_lattice lat = new (std::nothrow) dcrf_lattice_s();
+    if (!lat) return DCRF_E_NOMEM;
+    lat->d = d;
+    lat->n = n;
+    lat->batch = batch;
+    lat->point_off.assign(offsets, offsets + batch + 1);
+    const int D1 = d + 1;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&lat->point_off_d, (batch + 1) * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&lat->vert_off_d, (batch + 1) * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&lat->pvid, (n > 0 ? n : 1) * D1 * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&lat->pbary, (n > 0 ? n : 1) * D1 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&lat->ones, (n > 0 ? n : 1) * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&lat->status, sizeof(int));
+    if (e != cudaSuccess) { lattice_free(lat); return DCRF_E_NOMEM; }
+    e = cudaMemcpyAsync(lat->point_off_d, offsets, (batch + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(lat->status, 0, sizeof(int), s);
+    if (e != cudaSuccess) { lattice_free(lat); return DCRF_E_CUDA; }
+    dcrf_status st;
+    switch (d) {
+    case 1: st = build_typed<1>(lat, features, s); break;
+    case 2: st = build_typed<2>(lat, features, s); break;
+    case 3: st = build_typed<3>(lat, features, s); break;
+    case 4: st = build_typed<4>(lat, features, s); break;
+    case 5: st = build_typed<5>(lat, features, s); break;
+    case 6: st = build_typed<6>(lat, features, s); break;
+    case 7: st = build_typed<7>(lat, features, s); break;
+    default: st = build_typed<8>(lat, features, s); break;
+    }
+    if (st != DCRF_OK) {
+        cudaStreamSynchronize(s);
+        lattice_free(lat);
+        return st;
+    }
+    *out = lat;
+    return DCRF_OK;
+}
+
+extern "C" dcrf_status dcrf_lattice_build(const float *features, int64_t n, int d, dcrf_stream stream,
+                                          dcrf_lattice *out) {
+    int64_t off[2] = {0, n};
+    if (n < 0) return DCRF_E_INVAL;
+    return dcrf_lattice_build_batch(features, off, 1, d, stream, out);
+}
+
+extern "C" dcrf_status dcrf_lattice_destroy(dcrf_lattice lat) {
+    if (!lat) return DCRF_E_INVAL;
+    cudaDeviceSynchronize();
+    lattice_free(lat);
+    return DCRF_OK;
+}
+
+extern "C" dcrf_status dcrf_lattice_info(dcrf_lattice lat, int64_t *n, int *d, int64_t *m, int *batch) {
+    if (!lat) return DCRF_E_INVAL;
+    if (n) *n = lat->n;
+    if (d) *d = lat->d;
+    if (m) *m = lat->m;
+    if (batch) *batch = lat->batch;
+    return DCRF_OK;
+}
+
+extern "C" dcrf_status dcrf_lattice_vertex_offsets(dcrf_lattice lat, int64_t *offsets) {
+    if (!lat || !offsets) return DCRF_E_INVAL;
+    for (int b = 0; b <= lat->batch; ++b) offsets[b] = lat->vert_off[b];
+    return DCRF_OK;
+}
+
+extern "C" dcrf_status dcrf_lattice_status(dcrf_lattice lat, dcrf_stream stream) {
+    if (!lat) return DCRF_E_INVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int h = 0;
+    DCRF_TRY(cudaMemcpyAsync(&h, lat->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DCRF_TRY(cudaMemsetAsync(lat->status, 0, sizeof(int), s));
+    DCRF_TRY(cudaStreamSynchronize(s));
+    return (dcrf_status)h;
+}
+
+extern "C" dcrf_status dcrf_lattice_export(dcrf_lattice lat, int32_t *keys, int32_t *point_vertex,
+                                           float *point_weight, int32_t *neighbours, dcrf_stream stream) {
+    if (!lat) return DCRF_E_INVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int D1 = lat->d + 1;
+    if (keys && lat->m)
+        DCRF_TRY(cudaMemcpyAsync(keys, lat->keys, lat->m * lat->d * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    if (point_vertex && lat->n)
+        DCRF_TRY(cudaMemcpyAsync(point_vertex, lat->pvid, lat->n * D1 * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    if (point_weight && lat->n)
+        DCRF_TRY(cudaMemcpyAsync(point_weight, lat->pbary, lat->n * D1 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    if (neighbours && lat->m)
+        DCRF_TRY(cudaMemcpyAsync(neighbours, lat->nbr, lat->m * D1 * 2 * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    return DCRF_OK;
+}

@@ -1,0 +1,672 @@
+// LP relaxation: subgradient by sort + divide and conquer, projected subgradient.
+//
+// Section 6 of the paper (Eq. 18-20), Appendix D (reformulation), Appendix E
+// (divide and conquer) and Algorithm 3, Potts model.
+//
+// For label i the pixels of every image are ranked by descending y(i), ties by
+// ascending pixel index.  With B = ceil(log2 n) levels, at level l the node of
+// a pixel is rank >> (B - l) and it lies in the right child when bit B-l-1 of
+// its rank is set.  Each node's lattice is the global lattice restricted to
+// the vertices its own points touch: a "tagged vertex" (label, vertex, node).
+// All tagged vertices of a level are found without hashing: the incidence
+// list (label, point, corner) is sorted once by (label, vertex, rank); at any
+// level the entries of one tagged vertex are then a contiguous run, and the
+// blur neighbour (label, v +- w_j, node) is the run of vertex v +- w_j whose
+// ranks fall in the node, found by binary search inside that vertex's group.
+// Per level: splat the right-child indicator into the runs, d+1 Jacobi blur
+// passes over the runs, slice at the left-child points into U.
+// Finally G = phi + 2U - c and S_LP = <y, G>.
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
+#include <cub/device/device_segmented_radix_sort.cuh>
+
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace {
+
+inline unsigned nb(int64_t work, int threads) { return (unsigned)((work + threads - 1) / threads); }
+
+inline int ceil_log2(int64_t n) {
+    int b = 0;
+    while ((1ll << b) < n) ++b;
+    return b;
+}
+
+// keys[i][a] = y_a(i) (with -0 folded into +0), vals[i][a] = a
+__global__ void k_lp_transpose(const float *__restrict__ Y, int64_t n, int L, float *__restrict__ keys,
+                               int32_t *__restrict__ vals, int *status) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n * L) return;
+    const int64_t a = q / L;
+    const int i = (int)(q - a * L);
+    float v = Y[q];
+    if (!isfinite(v)) dcrf_flag(status, DCRF_E_NONFINITE);
+    keys[(int64_t)i * n + a] = v + 0.0f;
+    vals[(int64_t)i * n + a] = (int32_t)a;
+}
+
+// seg offsets for (label, image): begin = i*n + off[b]
+__global__ void k_lp_segments(const int64_t *__restrict__ off, int batch, int L, int64_t n,
+                              int64_t *__restrict__ begin, int64_t *__restrict__ end) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= L * batch) return;
+    const int i = s / batch, b = s - i * batch;
+    begin[s] = (int64_t)i * n + off[b];
+    end[s] = (int64_t)i * n + off[b + 1];
+}
+
+// rankpos[i][a] = position p of a in label i's sorted list (global within the label row)
+__global__ void k_lp_inverse(const int32_t *__restrict__ perm, int64_t n, int L, int32_t *__restrict__ inv) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n * L) return;
+    const int64_t i = q / n;
+    inv[i * n + perm[q]] = (int32_t)(q - i * n);
+}
+
+// Entries in (label, position, corner) order: key = label * M + vertex.
+__global__ void k_lp_entries(const int32_t *__restrict__ perm, int64_t n, int L, int d1,
+                             const int32_t *__restrict__ pvid, int64_t m, uint64_t *__restrict__ key,
+                             int32_t *__restrict__ q_out) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t E = n * L * d1;
+    if (q >= E) return;
+    const int64_t ip = q / d1;
+    const int k = (int)(q - ip * d1);
+    const int64_t i = ip / n;
+    const int32_t a = perm[ip];
+    const int v = pvid[(int64_t)a * d1 + k];
+    key[q] = (uint64_t)i * (uint64_t)m + (uint64_t)(v < 0 ? 0 : v);
+    q_out[q] = (int32_t)q;
+}
+
+// After the sort: per entry its vertex, rank, weight, and pos[q] = e.
+__global__ void k_lp_unpack(const uint64_t *__restrict__ key_s, const int32_t *__restrict__ q_s, int64_t E,
+                            int64_t n, int d1, int64_t m, const int32_t *__restrict__ perm,
+                            const int64_t *__restrict__ point_off, int batch, const float *__restrict__ pbary,
+                            int32_t *__restrict__ vid_s, int32_t *__restrict__ rank_s,
+                            float *__restrict__ bary_s, int32_t *__restrict__ pos) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    const int64_t q = q_s[e];
+    const int64_t ip = q / d1;
+    const int k = (int)(q - ip * d1);
+    const int64_t p = ip % n;
+    const int32_t a = perm[ip];
+    int lo = 0, hi = batch - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (point_off[mid] <= p) lo = mid; else hi = mid - 1;
+    }
+    vid_s[e] = (int32_t)(key_s[e] % (uint64_t)m);
+    rank_s[e] = (int32_t)(p - point_off[lo]);
+    bary_s[e] = pbary[(int64_t)a * d1 + k];
+    pos[q] = (int32_t)e;
+}
+
+struct LevelArgs {
+    const int32_t *vid_s;
+    const int32_t *rank_s;
+    const float *bary_s;
+    const int32_t *vimg;      // [m]
+    const int32_t *nlev;      // [batch] levels per image
+    const int64_t *csr;       // [m+1] incidence offsets of every vertex (label-independent)
+    const int32_t *nbr;       // [m][d1][2]
+    int64_t E, n, m;
+    int d1, level;
+};
+
+__device__ __forceinline__ bool entry_node(const LevelArgs &A, int64_t e, int32_t &node, int &bit) {
+    const int v = A.vid_s[e];
+    const int B = A.nlev[A.vimg[v]];
+    if (A.level >= B) return false;
+    const int r = A.rank_s[e];
+    node = r >> (B - A.level);
+    bit = (r >> (B - A.level - 1)) & 1;
+    return true;
+}
+
+__global__ void k_lp_flags(LevelArgs A, int32_t *__restrict__ flag) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= A.E) return;
+    int f = 1;
+    if (e > 0 && (e % (A.n * A.d1)) != 0 && A.vid_s[e] == A.vid_s[e - 1]) {
+        int32_t n0, n1;
+        int b0, b1;
+        const bool a0 = entry_node(A, e, n0, b0), a1 = entry_node(A, e - 1, n1, b1);
+        f = (a0 && a1 && n0 == n1) ? 0 : 1;
+    }
+    flag[e] = f;
+}
+
+__global__ void k_lp_splat(LevelArgs A, const int32_t *__restrict__ flag, const int32_t *__restrict__ rid,
+                           float *__restrict__ val, int32_t *__restrict__ run_first) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= A.E) return;
+    const int32_t r = rid[e] - 1;   // inclusive scan of run starts
+    if (flag[e]) run_first[r] = (int32_t)e;
+    int32_t node;
+    int bit;
+    if (entry_node(A, e, node, bit) && bit) atomicAdd(val + r, A.bary_s[e]);
+}
+
+// rnbr[r][j][side]: the run of (label, v -+ w_j, node) or -1.
+__global__ void k_lp_neighbours(LevelArgs A, const int32_t *__restrict__ run_first, int64_t R,
+                                const int32_t *__restrict__ rid, int32_t *__restrict__ rnbr) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const int64_t e0 = run_first[r];
+    int32_t node;
+    int bit;
+    const bool active = entry_node(A, e0, node, bit);
+    const int v = A.vid_s[e0];
+    const int64_t label_base = (e0 / (A.n * A.d1)) * (A.n * A.d1);
+    const int B = A.nlev[A.vimg[v]];
+    const int shift = B - A.level;
+    for (int j = 0; j < A.d1; ++j) {
+        for (int side = 0; side < 2; ++side) {
+            int32_t out = -1;
+            const int u = A.nbr[((int64_t)v * A.d1 + j) * 2 + side];
+            if (active && u >= 0) {
+                int64_t lo = label_base + A.csr[u], hi = label_base + A.csr[u + 1];
+                const int64_t end = hi;
+                while (lo < hi) {   // first entry with rank >> shift >= node
+                    const int64_t mid = (lo + hi) >> 1;
+                    if ((A.rank_s[mid] >> shift) < node) lo = mid + 1; else hi = mid;
+                }
+                if (lo < end && (A.rank_s[lo] >> shift) == node) out = rid[lo] - 1;
+            }
+            rnbr[(r * A.d1 + j) * 2 + side] = out;
+        }
+    }
+}
+
+__global__ void k_lp_blur(const float *__restrict__ in, float *__restrict__ out, const int32_t *__restrict__ rnbr,
+                          int64_t R, int d1, int j) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const int2 nbv = reinterpret_cast<const int2 *>(rnbr)[r * d1 + j];
+    float v = 0.5f * in[r];
+    if (nbv.x >= 0) v += 0.25f * in[nbv.x];
+    if (nbv.y >= 0) v += 0.25f * in[nbv.y];
+    out[r] = v;
+}
+
+// U[i][p] += ws0 * sum_k b_k val[run of (i, p, k)] for left-child positions.
+__global__ void k_lp_slice(LevelArgs A, const int32_t *__restrict__ pos, const int32_t *__restrict__ rid,
+                           const float *__restrict__ val, float ws0, float *__restrict__ U) {
+    int64_t ip = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t total = A.E / A.d1;
+    if (ip >= total) return;
+    const int64_t e0 = pos[ip * A.d1];
+    int32_t node;
+    int bit;
+    if (!entry_node(A, e0, node, bit) || bit) return;
+    float acc = 0.f;
+    for (int k = 0; k < A.d1; ++k) {
+        const int64_t e = pos[ip * A.d1 + k];
+        acc += A.bary_s[e] * val[rid[e] - 1];
+    }
+    U[ip] += ws0 * acc;
+}
+
+__global__ void k_lp_csr_count(const int32_t *__restrict__ pvid, int64_t count, unsigned *__restrict__ cnt) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < count) {
+        const int v = pvid[q];
+        if (v >= 0) atomicAdd(cnt + v, 1u);
+    }
+}
+
+__global__ void k_lp_combine(const float *__restrict__ phi, const float *__restrict__ Y, const float *__restrict__ U,
+                             const int32_t *__restrict__ inv, const float *__restrict__ c, int64_t n, int L,
+                             const int64_t *__restrict__ off, int batch, float *__restrict__ G,
+                             double *__restrict__ energy) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double part = 0.0;
+    int img = -1;
+    if (q < n * L) {
+        const int64_t a = q / L;
+        const int i = (int)(q - a * L);
+        const float g = phi[q] + 2.f * U[(int64_t)i * n + inv[(int64_t)i * n + a]] - c[a];
+        G[q] = g;
+        part = (double)Y[q] * g;
+        int lo = 0, hi = batch - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= a) lo = mid; else hi = mid - 1;
+        }
+        img = lo;
+    }
+    if (energy) {
+        // one atomic per warp when the warp lies in one image
+        const int lane = threadIdx.x & 31;
+        const int img0 = __shfl_sync(0xffffffffu, img, 0);
+        const bool uni = __all_sync(0xffffffffu, img == img0 || img < 0);
+        if (uni) {
+            double sum = part;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+            if (lane == 0 && img0 >= 0) atomicAdd(energy + img0, sum);
+        } else if (img >= 0) {
+            atomicAdd(energy + img, part);
+        }
+    }
+}
+
+__global__ void k_lp_c(int64_t n, const float *const *ones, const float *w, int nk, float sumw, float *c) {
+    int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    float s = 0.f;
+    for (int m = 0; m < nk; ++m) s += w[m] * ones[m][a];
+    s -= sumw;
+    c[a] = s > 0.f ? s : 0.f;
+}
+
+// Euclidean projection of one row onto the simplex by Michelot's active-set
+// iteration: tau = (sum_{active} v - 1)/|active|, drop v_i <= tau, repeat.
+template <int LP>
+__global__ void k_project(const float *__restrict__ V, int64_t n, int L, const float *__restrict__ G,
+                          const double *__restrict__ step, const int64_t *__restrict__ off, int batch,
+                          float *__restrict__ Y) {
+    int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    float beta = 0.f;
+    if (G) {
+        int lo = 0, hi = batch - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= a) lo = mid; else hi = mid - 1;
+        }
+        beta = (float)step[lo];
+    }
+    float v[LP];
+    bool act[LP];
+#pragma unroll
+    for (int i = 0; i < LP; ++i) {
+        v[i] = i < L ? V[a * L + i] - (G ? beta * G[a * L + i] : 0.f) : 0.f;
+        act[i] = i < L;
+    }
+    float tau = 0.f;
+    for (int it = 0; it <= L; ++it) {
+        float s = 0.f;
+        int cnt = 0;
+#pragma unroll
+        for (int i = 0; i < LP; ++i)
+            if (act[i]) { s += v[i]; ++cnt; }
+        tau = (s - 1.f) / (float)cnt;
+        bool changed = false;
+#pragma unroll
+        for (int i = 0; i < LP; ++i)
+            if (act[i] && v[i] <= tau) { act[i] = false; changed = true; }
+        if (!changed) break;
+    }
+#pragma unroll
+    for (int i = 0; i < LP; ++i)
+        if (i < L) Y[a * L + i] = act[i] ? v[i] - tau : 0.f;
+}
+
+dcrf_status launch_project(const float *V, int64_t n, int L, const float *G, const double *step,
+                           const int64_t *off, int batch, float *Y, cudaStream_t s) {
+    if (n == 0) return DCRF_OK;
+    ProfScope ps(P_LP_PROJECT, s);
+    if (L <= 8) k_project<8><<<nb(n, 128), 128, 0, s>>>(V, n, L, G, step, off, batch, Y);
+    else if (L <= 24) k_project<24><<<nb(n, 128), 128, 0, s>>>(V, n, L, G, step, off, batch, Y);
+    else k_project<64><<<nb(n, 128), 128, 0, s>>>(V, n, L, G, step, off, batch, Y);
+    DCRF_LAUNCHED();
+    return DCRF_OK;
+}
+
+// Reusable workspace of the subgradient for one set of lattices.
+struct LpWork {
+    cudaStream_t s;
+    Scratch sc;
+    const dcrf_lattice *lats = nullptr;
+    int nk = 0, L = 0, batch = 0;
+    int64_t n = 0;
+    float sumw = 0.f;
+    float ws0[DCRF_MAX_KERNELS];
+    int64_t *off_d = nullptr, *seg_b = nullptr, *seg_e = nullptr;
+    int32_t *nlev_d = nullptr;
+    int maxlev = 0;
+    float *c = nullptr;
+    float *keys = nullptr, *keys2 = nullptr;
+    int32_t *vals = nullptr, *perm = nullptr, *inv = nullptr;
+    float *U = nullptr;
+    int64_t *csr[DCRF_MAX_KERNELS] = {};
+    int64_t Emax = 0;
+    uint64_t *ekey = nullptr, *ekey2 = nullptr;
+    int32_t *eq = nullptr, *eq2 = nullptr, *vid_s = nullptr, *rank_s = nullptr, *pos = nullptr;
+    int32_t *flag = nullptr, *rid = nullptr, *run_first = nullptr, *rnbr = nullptr;
+    float *bary_s = nullptr, *val = nullptr, *val2 = nullptr;
+    void *tmp = nullptr;
+    size_t tmp_bytes = 0;
+
+    explicit LpWork(cudaStream_t st) : s(st), sc(st) {}
+
+    dcrf_status setup(const dcrf_lattice *lattices, const float *weights, int n_k, int L_) {
+        DCRF_CHECK_STATUS(dcrf_check_lattices(lattices, n_k));
+        if (!weights || L_ < 1 || L_ > DCRF_MAX_L) return DCRF_E_INVAL;
+        lats = lattices;
+        nk = n_k;
+        L = L_;
+        n = lattices[0]->n;
+        batch = lattices[0]->batch;
+        sumw = 0.f;
+        for (int m = 0; m < nk; ++m) {
+            if (!(weights[m] >= 0.f)) return DCRF_E_INVAL;
+            sumw += weights[m];
+            ws0[m] = (float)(weights[m] * lattices[m]->s0);
+            Emax = std::max<int64_t>(Emax, n * L * (lattices[m]->d + 1));
+        }
+        if (Emax >= (1ll << 31)) return DCRF_E_INVAL;
+        std::vector<int32_t> nlev(batch);
+        for (int b = 0; b < batch; ++b) {
+            nlev[b] = ceil_log2(lattices[0]->point_off[b + 1] - lattices[0]->point_off[b]);
+            maxlev = std::max(maxlev, (int)nlev[b]);
+        }
+        DCRF_CHECK_STATUS(sc.get(&off_d, batch + 1));
+        DCRF_CHECK_STATUS(sc.get(&nlev_d, batch));
+        DCRF_CHECK_STATUS(sc.get(&seg_b, (size_t)L * batch));
+        DCRF_CHECK_STATUS(sc.get(&seg_e, (size_t)L * batch));
+        DCRF_TRY(cudaMemcpyAsync(off_d, lattices[0]->point_off.data(), (batch + 1) * sizeof(int64_t),
+                                 cudaMemcpyHostToDevice, s));
+        DCRF_TRY(cudaMemcpyAsync(nlev_d, nlev.data(), batch * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        k_lp_segments<<<nb(L * batch, 128), 128, 0, s>>>(off_d, batch, L, n, seg_b, seg_e);
+        DCRF_LAUNCHED();
+        const size_t nl = (size_t)(n > 0 ? n : 1) * L;
+        DCRF_CHECK_STATUS(sc.get(&c, (size_t)(n > 0 ? n : 1)));
+        DCRF_CHECK_STATUS(sc.get(&keys, nl));
+        DCRF_CHECK_STATUS(sc.get(&keys2, nl));
+        DCRF_CHECK_STATUS(sc.get(&vals, nl));
+        DCRF_CHECK_STATUS(sc.get(&perm, nl));
+        DCRF_CHECK_STATUS(sc.get(&inv, nl));
+        DCRF_CHECK_STATUS(sc.get(&U, nl));
+        const size_t ne = (size_t)(Emax > 0 ? Emax : 1);
+        DCRF_CHECK_STATUS(sc.get(&ekey, ne));
+        DCRF_CHECK_STATUS(sc.get(&ekey2, ne));
+        DCRF_CHECK_STATUS(sc.get(&eq, ne));
+        DCRF_CHECK_STATUS(sc.get(&eq2, ne));
+        DCRF_CHECK_STATUS(sc.get(&vid_s, ne));
+        DCRF_CHECK_STATUS(sc.get(&rank_s, ne));
+        DCRF_CHECK_STATUS(sc.get(&pos, ne));
+        DCRF_CHECK_STATUS(sc.get(&flag, ne));
+        DCRF_CHECK_STATUS(sc.get(&rid, ne));
+        DCRF_CHECK_STATUS(sc.get(&run_first, ne));
+        DCRF_CHECK_STATUS(sc.get(&bary_s, ne));
+        DCRF_CHECK_STATUS(sc.get(&val, ne));
+        DCRF_CHECK_STATUS(sc.get(&val2, ne));
+        int dmax = 1;
+        for (int m = 0; m < nk; ++m) dmax = std::max(dmax, lattices[m]->d + 1);
+        DCRF_CHECK_STATUS(sc.get(&rnbr, ne * dmax * 2));
+        // temp storage for the sorts and scans
+        size_t t1 = 0, t2 = 0, t3 = 0;
+        DCRF_TRY(cub::DeviceSegmentedRadixSort::SortPairsDescending(nullptr, t1, keys, keys2, vals, perm, (int)nl,
+                                                                     L * batch, seg_b, seg_e, 0, 32, s));
+        DCRF_TRY(cub::DeviceRadixSort::SortPairs(nullptr, t2, ekey, ekey2, eq, eq2, (int)ne, 0, 64, s));
+        DCRF_TRY(cub::DeviceScan::InclusiveSum(nullptr, t3, flag, rid, (int)ne, s));
+        tmp_bytes = std::max(t1, std::max(t2, t3));
+        char *t;
+        DCRF_CHECK_STATUS(sc.get(&t, tmp_bytes));
+        tmp = t;
+        // incidence offsets per vertex (label independent)
+        for (int m = 0; m < nk; ++m) {
+            const dcrf_lattice lat = lattices[m];
+            unsigned *cnt;
+            DCRF_CHECK_STATUS(sc.get(&cnt, (size_t)lat->m + 1));
+            DCRF_CHECK_STATUS(sc.get(&csr[m], (size_t)lat->m + 1));
+            DCRF_TRY(cudaMemsetAsync(cnt, 0, (lat->m + 1) * sizeof(unsigned), s));
+            if (n > 0) {
+                k_lp_csr_count<<<nb(n * (lat->d + 1), 256), 256, 0, s>>>(lat->pvid, n * (lat->d + 1), cnt);
+                DCRF_LAUNCHED();
+            }
+            size_t tb = 0;
+            DCRF_TRY(cub::DeviceScan::ExclusiveSum(nullptr, tb, cnt, csr[m], (int)(lat->m + 1), s));
+            char *tt;
+            DCRF_CHECK_STATUS(sc.get(&tt, tb));
+            DCRF_TRY(cub::DeviceScan::ExclusiveSum(tt, tb, cnt, csr[m], (int)(lat->m + 1), s));
+        }
+        // c_a
+        const float *ones_h[DCRF_MAX_KERNELS];
+        for (int m = 0; m < nk; ++m) ones_h[m] = lattices[m]->ones;
+        const float **ones_d;
+        float *w_d;
+        DCRF_CHECK_STATUS(sc.get(&ones_d, nk));
+        DCRF_CHECK_STATUS(sc.get(&w_d, nk));
+        DCRF_TRY(cudaMemcpyAsync(ones_d, ones_h, nk * sizeof(float *), cudaMemcpyHostToDevice, s));
+        DCRF_TRY(cudaMemcpyAsync(w_d, weights, nk * sizeof(float), cudaMemcpyHostToDevice, s));
+        if (n > 0) {
+            k_lp_c<<<nb(n, 256), 256, 0, s>>>(n, ones_d, w_d, nk, sumw, c);
+            DCRF_LAUNCHED();
+        }
+        return DCRF_OK;
+    }
+
+    // G = phi + 2U - c; energy[b] += <y, G> over image b (energy zeroed by caller)
+    dcrf_status subgrad(const float *phi, const float *Y, float *G, double *energy) {
+        if (n == 0) return DCRF_OK;
+        const int64_t nl = n * L;
+        const int status_lat = 0;
+        (void)status_lat;
+        {
+            ProfScope ps(P_LP_SORT, s);
+            k_lp_transpose<<<nb(nl, 256), 256, 0, s>>>(Y, n, L, keys, vals, lats[0]->status);
+            DCRF_LAUNCHED();
+            size_t tb = tmp_bytes;
+            DCRF_TRY(cub::DeviceSegmentedRadixSort::SortPairsDescending(tmp, tb, keys, keys2, vals, perm, (int)nl,
+                                                                         L * batch, seg_b, seg_e, 0, 32, s));
+            k_lp_inverse<<<nb(nl, 256), 256, 0, s>>>(perm, n, L, inv);
+            DCRF_LAUNCHED();
+        }
+        DCRF_TRY(cudaMemsetAsync(U, 0, nl * sizeof(float), s));
+        for (int mm = 0; mm < nk; ++mm) {
+            const dcrf_lattice lat = lats[mm];
+            const int d1 = lat->d + 1;
+            const int64_t E = nl * d1;
+            const int64_t m = lat->m > 0 ? lat->m : 1;
+            int keybits = 1;
+            while (keybits < 64 && ((uint64_t)L * (uint64_t)m) > (1ull << keybits)) ++keybits;
+            {
+                ProfScope ps(P_LP_SORT, s);
+                k_lp_entries<<<nb(E, 256), 256, 0, s>>>(perm, n, L, d1, lat->pvid, m, ekey, eq);
+                DCRF_LAUNCHED();
+                size_t tb = tmp_bytes;
+                DCRF_TRY(cub::DeviceRadixSort::SortPairs(tmp, tb, ekey, ekey2, eq, eq2, (int)E, 0, keybits, s));
+                k_lp_unpack<<<nb(E, 256), 256, 0, s>>>(ekey2, eq2, E, n, d1, m, perm, off_d, batch, lat->pbary,
+                                                       vid_s, rank_s, bary_s, pos);
+                DCRF_LAUNCHED();
+            }
+            LevelArgs A;
+            A.vid_s = vid_s;
+            A.rank_s = rank_s;
+            A.bary_s = bary_s;
+            A.vimg = lat->vimg;
+            A.nlev = nlev_d;
+            A.csr = csr[mm];
+            A.nbr = lat->nbr;
+            A.E = E;
+            A.n = n;
+            A.m = m;
+            A.d1 = d1;
+            for (int lev = 0; lev < maxlev; ++lev) {
+                A.level = lev;
+                {
+                    ProfScope ps(P_LP_RUNS, s);
+                    k_lp_flags<<<nb(E, 256), 256, 0, s>>>(A, flag);
+                    DCRF_LAUNCHED();
+                    size_t tb = tmp_bytes;
+                    DCRF_TRY(cub::DeviceScan::InclusiveSum(tmp, tb, flag, rid, (int)E, s));
+                }
+                // rid[e] = 1 + run of entry e; the number of runs is rid[E-1]
+                int32_t last = 0;
+                DCRF_TRY(cudaMemcpyAsync(&last, rid + E - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+                DCRF_TRY(cudaStreamSynchronize(s));
+                const int64_t R = (int64_t)last;
+                DCRF_TRY(cudaMemsetAsync(val, 0, R * sizeof(float), s));
+                {
+                    ProfScope ps(P_LP_SPLAT, s);
+                    k_lp_splat<<<nb(E, 256), 256, 0, s>>>(A, flag, rid, val, run_first);
+                    DCRF_LAUNCHED();
+                }
+                {
+                    ProfScope ps(P_LP_NEIGHBOURS, s);
+                    k_lp_neighbours<<<nb(R, 128), 128, 0, s>>>(A, run_first, R, rid, rnbr);
+                    DCRF_LAUNCHED();
+                }
+                float *in = val, *out = val2;
+                for (int j = 0; j < d1; ++j) {
+                    ProfScope ps(P_LP_BLUR, s);
+                    k_lp_blur<<<nb(R, 256), 256, 0, s>>>(in, out, rnbr, R, d1, j);
+                    DCRF_LAUNCHED();
+                    std::swap(in, out);
+                }
+                {
+                    ProfScope ps(P_LP_SLICE, s);
+                    k_lp_slice<<<nb(nl, 256), 256, 0, s>>>(A, pos, rid, in, ws0[mm], U);
+                    DCRF_LAUNCHED();
+                }
+            }
+        }
+        {
+            ProfScope ps(P_LP_COMBINE, s);
+            k_lp_combine<<<nb(nl, 256), 256, 0, s>>>(phi, Y, U, inv, c, n, L, off_d, batch, G, energy);
+            DCRF_LAUNCHED();
+        }
+        return DCRF_OK;
+    }
+};
+
+__global__ void k_lp_beta0(const float *__restrict__ G, int64_t n, int L, const int64_t *__restrict__ off,
+                           int batch, unsigned *__restrict__ maxdev) {
+    int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    float mean = 0.f;
+    for (int i = 0; i < L; ++i) mean += G[a * L + i];
+    mean /= (float)L;
+    float dev = 0.f;
+    for (int i = 0; i < L; ++i) dev = fmaxf(dev, fabsf(G[a * L + i] - mean));
+    int lo = 0, hi = batch - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= a) lo = mid; else hi = mid - 1;
+    }
+    atomicMax(maxdev + lo, __float_as_uint(dev));   // non-negative floats order as their bits
+}
+
+__global__ void k_lp_steps(const unsigned *__restrict__ maxdev, double beta0, int batch, double *__restrict__ b0) {
+    for (int b = threadIdx.x; b < batch; b += blockDim.x) {
+        if (beta0 > 0.0) { b0[b] = beta0; continue; }
+        const float dv = __uint_as_float(maxdev[b]);
+        b0[b] = dv > 0.f ? 0.1 / (double)dv : 0.1;
+    }
+}
+
+__global__ void k_lp_scale(const double *__restrict__ b0, double factor, int batch, double *__restrict__ step) {
+    for (int b = threadIdx.x; b < batch; b += blockDim.x) step[b] = b0[b] * factor;
+}
+
+// keep the best iterate per image: if e[b] < best[b] copy image b's rows
+__global__ void k_lp_keep_best(const double *__restrict__ e, double *__restrict__ best, int batch,
+                               int *__restrict__ take) {
+    for (int b = threadIdx.x; b < batch; b += blockDim.x) {
+        take[b] = e[b] < best[b];
+        if (take[b]) best[b] = e[b];
+    }
+}
+
+__global__ void k_lp_copy_rows(const float *__restrict__ src, float *__restrict__ dst, int64_t n, int L,
+                               const int64_t *__restrict__ off, int batch, const int *__restrict__ take) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n * L) return;
+    const int64_t a = q / L;
+    int lo = 0, hi = batch - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= a) lo = mid; else hi = mid - 1;
+    }
+    if (!take || take[lo]) dst[q] = src[q];
+}
+
+}  // namespace
+
+extern "C" dcrf_status dcrf_lp_subgrad(const float *unaries, const float *Y, const dcrf_lattice *lattices,
+                                       const float *weights, int n_kernels, int L, float *G, double *energy,
+                                       dcrf_stream stream) {
+    if (!unaries || !Y || !G) return DCRF_E_INVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    LpWork W(s);
+    DCRF_CHECK_STATUS(W.setup(lattices, weights, n_kernels, L));
+    double *e;
+    DCRF_CHECK_STATUS(W.sc.get(&e, (size_t)W.batch));
+    DCRF_TRY(cudaMemsetAsync(e, 0, W.batch * sizeof(double), s));
+    DCRF_CHECK_STATUS(W.subgrad(unaries, Y, G, e));
+    if (energy) {
+        DCRF_TRY(cudaMemcpyAsync(energy, e, W.batch * sizeof(double), cudaMemcpyDeviceToHost, s));
+        int h = 0;
+        DCRF_TRY(cudaMemcpyAsync(&h, lattices[0]->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        DCRF_TRY(cudaStreamSynchronize(s));
+        if (h != 0) return (dcrf_status)h;
+    }
+    return DCRF_OK;
+}
+
+extern "C" dcrf_status dcrf_lp_solve(const float *unaries, const dcrf_lattice *lattices, const float *weights,
+                                     int n_kernels, int L, int steps, double beta0, float *Y, double *energies,
+                                     dcrf_stream stream) {
+    if (!unaries || !Y || steps < 0) return DCRF_E_INVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    LpWork W(s);
+    DCRF_CHECK_STATUS(W.setup(lattices, weights, n_kernels, L));
+    if (W.n == 0) return DCRF_OK;
+    const int batch = W.batch;
+    const int64_t nl = W.n * L;
+    float *G, *Yb;
+    double *e, *best, *b0, *step;
+    unsigned *maxdev;
+    int *take;
+    DCRF_CHECK_STATUS(W.sc.get(&G, (size_t)nl));
+    DCRF_CHECK_STATUS(W.sc.get(&Yb, (size_t)nl));
+    DCRF_CHECK_STATUS(W.sc.get(&e, (size_t)(steps + 1) * batch));
+    DCRF_CHECK_STATUS(W.sc.get(&best, (size_t)batch));
+    DCRF_CHECK_STATUS(W.sc.get(&b0, (size_t)batch));
+    DCRF_CHECK_STATUS(W.sc.get(&step, (size_t)batch));
+    DCRF_CHECK_STATUS(W.sc.get(&maxdev, (size_t)batch));
+    DCRF_CHECK_STATUS(W.sc.get(&take, (size_t)batch));
+    DCRF_TRY(cudaMemsetAsync(e, 0, (steps + 1) * batch * sizeof(double), s));
+    DCRF_TRY(cudaMemsetAsync(maxdev, 0, batch * sizeof(unsigned), s));
+    DCRF_CHECK_STATUS(W.subgrad(unaries, Y, G, e));
+    DCRF_TRY(cudaMemcpyAsync(best, e, batch * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    DCRF_TRY(cudaMemcpyAsync(Yb, Y, nl * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    k_lp_beta0<<<nb(W.n, 256), 256, 0, s>>>(G, W.n, L, W.off_d, batch, maxdev);
+    DCRF_LAUNCHED();
+    k_lp_steps<<<1, 256, 0, s>>>(maxdev, beta0, batch, b0);
+    DCRF_LAUNCHED();
+    for (int t = 0; t < steps; ++t) {
+        k_lp_scale<<<1, 256, 0, s>>>(b0, 1.0 / (1.0 + t), batch, step);
+        DCRF_LAUNCHED();
+        DCRF_CHECK_STATUS(launch_project(Y, W.n, L, G, step, W.off_d, batch, Y, s));
+        double *et = e + (int64_t)(t + 1) * batch;
+        DCRF_CHECK_STATUS(W.subgrad(unaries, Y, G, et));
+        k_lp_keep_best<<<1, 256, 0, s>>>(et, best, batch, take);
+        DCRF_LAUNCHED();
+        k_lp_copy_rows<<<nb(nl, 256), 256, 0, s>>>(Y, Yb, W.n, L, W.off_d, batch, take);
+        DCRF_LAUNCHED();
+    }
+    k_lp_copy_rows<<<nb(nl, 256), 256, 0, s>>>(Yb, Y, W.n, L, W.off_d, batch, nullptr);
+    DCRF_LAUNCHED();
+    if (energies) {
+        DCRF_TRY(cudaMemcpyAsync(energies, e, (steps + 1) * batch * sizeof(double), cudaMemcpyDeviceToHost, s));
+        int h = 0;
+        DCRF_TRY(cudaMemcpyAsync(&h, lattices[0]->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        DCRF_TRY(cudaStreamSynchronize(s));
+        if (h != 0) return (dcrf_status)h;
+    }
+    return DCRF_OK;
+}
+
+extern "C" dcrf_status dcrf_simplex_project(const float *V, int64_t n, int L, float *Y, dcrf_stream stream) {
+    if (!V || !Y || n < 0 || L < 1 || L > DCRF_MAX_L) return DCRF_E_INVAL;
+    return launch_project(V, n, L, nullptr, nullptr, nullptr, 1, Y, (cudaStream_t)stream);
+}

@@ -1,0 +1,113 @@
+"""GPU parity of Frank-Wolfe (Algorithm 1, Appendix B) and CCCP (Algorithm 2)."""
+import numpy as np
+import pytest
+
+from helpers import gpu_setup, oracle_crf, rel_err
+from oracle import qp
+from paper_1608_06192_gb300 import synthetic as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ENERGY_TOL = 1e-3
+
+
+def _run_fw(dcrf, probs, iters, storage="f32", mu=None):
+    g = gpu_setup(dcrf, probs, torch)
+    Y = g["y0"].clone()
+    rec = dcrf.dcrf_qp_fw(g["phi"], [g["lb"], g["ls"]], probs[0].weights, Y, iters, compat=mu, storage=storage)
+    return g, Y.cpu().numpy(), rec
+
+
+def _check_against_oracle(probs, g, Y, rec, iters, mu=None, tol=ENERGY_TOL):
+    for b, p in enumerate(probs):
+        c = oracle_crf(p, mu)
+        y_o, _, rec_o = qp.frank_wolfe(c, p.y0, iters)
+        e_o = rec_o[:, 0]
+        scale = np.abs(e_o).max()
+        # per-iteration energy and the final relaxed energy
+        assert np.abs(rec[:, b, 0] - e_o).max() <= tol * scale
+        s, e = g["off"][b], g["off"][b + 1]
+        assert abs(c.s_cvx(Y[s:e].astype(np.float64)) - c.s_cvx(y_o)) <= tol * abs(c.s_cvx(y_o))
+        # gap non-negative (to rounding) and the energy never rises
+        assert np.all(rec[:, b, 1] >= -1e-6 * scale)
+        assert np.all(np.diff(rec[:, b, 0]) <= 1e-6 * scale)
+        # the iterate stays on the simplex
+        np.testing.assert_allclose(Y[s:e].sum(1), 1.0, atol=1e-5)
+        assert Y[s:e].min() >= -1e-6
+
+
+def test_fw_small_fp32(dcrf):
+    p = S.qp_small()
+    g, Y, rec = _run_fw(dcrf, [p], 50)
+    _check_against_oracle([p], g, Y, rec, 50)
+
+
+def test_fw_small_fp16_storage(dcrf):
+    p = S.qp_small()
+    g, Y, rec = _run_fw(dcrf, [p], 50, storage="f16")
+    _check_against_oracle([p], g, Y, rec, 50)
+
+
+def test_fw_general_compatibility(dcrf):
+    p = S.make_problem(48, 40, 6, 4, seed=9)
+    rng = np.random.default_rng(1)
+    mu = rng.uniform(0.0, 1.5, (4, 4))
+    mu = (mu + mu.T) / 2
+    np.fill_diagonal(mu, 0.0)
+    g, Y, rec = _run_fw(dcrf, [p], 30, mu=mu)
+    _check_against_oracle([p], g, Y, rec, 30, mu=mu)
+
+
+def test_fw_batch_uneven(dcrf):
+    probs = [S.make_problem(w, h, 7, 5, seed=30 + i) for i, (w, h) in enumerate([(40, 30), (3, 2), (64, 17)])]
+    g, Y, rec = _run_fw(dcrf, probs, 25)
+    _check_against_oracle(probs, g, Y, rec, 25)
+
+
+def test_fw_headline_size(dcrf):
+    p = S.voc_shaped()
+    g, Y, rec = _run_fw(dcrf, [p], 8, storage="f16")
+    _check_against_oracle([p], g, Y, rec, 8)
+
+
+def test_fw_zero_iterations_leaves_y(dcrf):
+    p = S.qp_small()
+    g, Y, rec = _run_fw(dcrf, [p], 0)
+    np.testing.assert_array_equal(Y, p.y0)
+
+
+def test_cccp_medium(dcrf):
+    p = S.qp_cccp_medium()
+    g = gpu_setup(dcrf, [p], torch)
+    Y = g["y0"].clone()
+    # QP Frank-Wolfe first, then CCCP from its result (10 outer x 50 inner)
+    dcrf.dcrf_qp_fw(g["phi"], [g["lb"], g["ls"]], p.weights, Y, 50, records=False)
+    yq = Y.cpu().numpy().astype(np.float64)
+    e = dcrf.dcrf_dc_cccp(g["phi"], [g["lb"], g["ls"]], p.weights, Y, 10, 50)[:, 0]
+    c = oracle_crf(p)
+    y_o, _, _ = qp.frank_wolfe(c, p.y0, 50)
+    y_c, e_o = qp.cccp_dc_gen(c, y_o, 10, 50)
+    scale = np.abs(e_o).max()
+    assert np.all(np.diff(e) <= 1e-5 * scale)                    # monotone (Section 5.1)
+    assert abs(e[0] - c.s_qp(yq)) <= ENERGY_TOL * scale
+    assert abs(e[-1] - e_o[-1]) <= ENERGY_TOL * scale
+    yg = Y.cpu().numpy().astype(np.float64)
+    assert abs(c.s_qp(yg) - e[-1]) <= ENERGY_TOL * scale
+
+
+def test_fw_graph_path_matches_eager(dcrf):
+    # a non-default stream takes the captured two-iteration graph path
+    p = S.make_problem(64, 48, 5, 5, seed=12)
+    g = gpu_setup(dcrf, [p], torch)
+    Y1 = g["y0"].clone()
+    r1 = dcrf.dcrf_qp_fw(g["phi"], [g["lb"], g["ls"]], p.weights, Y1, 21)
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        Y2 = g["y0"].clone()
+        r2 = dcrf.dcrf_qp_fw(g["phi"], [g["lb"], g["ls"]], p.weights, Y2, 21, stream=s)
+    s.synchronize()
+    scale = np.abs(r1[:, 0, 0]).max()
+    assert np.abs(r1[:, 0, 0] - r2[:, 0, 0]).max() <= 1e-6 * scale
+    assert rel_err(Y2.cpu().numpy(), Y1.cpu().numpy()) <= 1e-4
