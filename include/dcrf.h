@@ -148,6 +148,23 @@ dcrf_status dcrf_qp_fw(const float *unaries, const dcrf_lattice *lattices, const
                        dcrf_fw_record *records, int storage, dcrf_stream stream);
 
 /*
+ * Reverse mode through `iters` unrolled Frank-Wolfe iterations (the
+ * differentiation pattern of this library; the paper names learning through
+ * its solvers as future work in its discussion).  Given dYT = dLoss/dy^T for
+ * y^T = dcrf_qp_fw(phi, w, y^0), returns dphi (device [N][L]), dY0 (device
+ * [N][L] or NULL) and dweights (host [n_kernels], summed over the batch, or
+ * NULL; when given the call synchronises).  The forward pass is recomputed
+ * from Y0 with float32 lattice values, checkpointing y^t and s^t of every
+ * iteration.  s^t is piecewise constant and alpha is constant where it is
+ * clipped to [0, 1]; elsewhere alpha = -B/(2A) is differentiated exactly,
+ * with Op^T applied through dcrf_filter_adjoint's reverse blur.
+ */
+dcrf_status dcrf_qp_fw_backward(const float *unaries, const dcrf_lattice *lattices, const float *weights,
+                                int n_kernels, const float *compat, int L, int iters, const float *Y0,
+                                const float *dYT, float *dphi, float *dY0, double *dweights,
+                                dcrf_stream stream);
+
+/*
  * CCCP on the generic DC relaxation (Section 5.1, Algorithm 2): outer steps
  * linearise q(y) = y^T D y at y^t and run `inner` Frank-Wolfe iterations on
  * phi^T y + y^T (Psi + D) y - 2 (d o y^t)^T y, warm-started at y^t.

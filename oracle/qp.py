@@ -73,3 +73,100 @@ def cccp_dc_gen(crf, y0, outer: int, inner: int):
         y, P_y, _ = frank_wolfe(crf, y, inner, lin=lin, P_y=P_y)
         energies.append(s_qp(y, P_y))
     return y, np.array(energies)
+
+
+# ---------------------------------------------------------------------------
+# Reverse mode through unrolled Frank-Wolfe (differentiation of T iterations)
+#
+# With P = Op(y) = (Psi + D) y exact, one iteration is
+#   y+ = y + alpha (s - y),  alpha = -B / (2A) when 0 < alpha < 1 and A > 0,
+# s piecewise constant in (y, phi, w) and alpha constant when clipped.  With
+# Delta = s - y and u = y - (1 - 2 alpha) Delta:
+#   d alpha / d y   = (lin + Op u + Op^T u) / (2A)
+#   d alpha / d phi = -Delta / (2A)
+#   d alpha / d w_m = -(dB_m + 2 alpha dA_m) / (2A),
+#     dA_m = <Delta, Op_m' Delta>,
+#     dB_m = -<d_m', Delta> + <y, Op_m' Delta> + <Delta, Op_m' y>,
+#   where Op_m' v = mu (K_m v - v) + d_m' o v is the derivative of Op in w_m and
+#   d_m' = (sum_j |mu_ij|) (K_m 1 - 1) [c > 0] that of d (lin = phi - d).
+# The adjoint step is  ybar <- (1 - alpha) ybar + abar d alpha/dy,  abar = <ybar, Delta>.
+
+
+class WeightedCRF:
+    """Dense CRF whose kernel weights are explicit: K = sum_m w_m K_m (K_m unweighted)."""
+
+    def __init__(self, unaries, ops, weights, mu=None):
+        """ops: per kernel (apply, apply_T) of the unweighted K_m (diagonal included)."""
+        from oracle.crf import potts
+        self.phi = np.asarray(unaries, dtype=np.float64)
+        self.n, self.L = self.phi.shape
+        self.ops = ops
+        self.w = np.asarray(weights, dtype=np.float64)
+        self.mu = potts(self.L) if mu is None else np.asarray(mu, dtype=np.float64)
+        self.musum = np.abs(self.mu).sum(axis=1)
+        ones = np.ones((self.n, 1))
+        self.o = [op(ones)[:, 0] for op, _ in ops]
+        c = sum(w * o for w, o in zip(self.w, self.o)) - self.w.sum()
+        self.active = c > 0
+        self.c = np.maximum(c, 0.0)
+        self.d = self.musum[None, :] * self.c[:, None]
+        self.dd = [self.musum[None, :] * ((o - 1.0) * self.active)[:, None] for o in self.o]
+
+    def op(self, v):
+        x = sum(w * f(v) for w, (f, _) in zip(self.w, self.ops)) - self.w.sum() * v
+        return x @ self.mu.T + self.d * v
+
+    def op_T(self, v):
+        x = sum(w * ft(v) for w, (_, ft) in zip(self.w, self.ops)) - self.w.sum() * v
+        return x @ self.mu + self.d * v
+
+    def dop(self, m, v):
+        return (self.ops[m][0](v) - v) @ self.mu.T + self.dd[m] * v
+
+    psi_plus_D = op
+
+
+def fw_tape(crf, y0, iters):
+    """Forward pass keeping y^t, s^t and (alpha, A, B) of every iteration."""
+    lin = crf.phi - crf.d
+    y = np.array(y0, dtype=np.float64)
+    P = crf.op(y)
+    rows = np.arange(crf.n)
+    tape = []
+    for _ in range(iters):
+        g = lin + 2.0 * P
+        s = np.zeros_like(y)
+        s[rows, np.argmin(g, axis=1)] = 1.0
+        Ps = crf.op(s)
+        delta, dP = s - y, Ps - P
+        A = float(np.sum(delta * dP))
+        B = float(np.sum(lin * delta) + np.sum(y * dP) + np.sum(delta * P))
+        alpha = step_size(A, B)
+        tape.append((y.copy(), s, alpha, A, B))
+        y = y + alpha * delta
+        P = P + alpha * dP
+    return y, tape
+
+
+def fw_backward(crf, tape, ybar):
+    """Gradients of <ybar, y^T> w.r.t. phi, the kernel weights and y^0."""
+    lin = crf.phi - crf.d
+    ybar = np.array(ybar, dtype=np.float64)
+    phibar = np.zeros_like(lin)
+    wbar = np.zeros(len(crf.w))
+    for y, s, alpha, A, B in reversed(tape):
+        delta = s - y
+        abar = float(np.sum(ybar * delta))
+        interior = A > 0.0 and 0.0 < alpha < 1.0
+        if interior:
+            u = y - (1.0 - 2.0 * alpha) * delta
+            da_dy = (lin + crf.op(u) + crf.op_T(u)) / (2.0 * A)
+            phibar += -abar * delta / (2.0 * A)
+            for m in range(len(crf.w)):
+                dA = float(np.sum(delta * crf.dop(m, delta)))
+                dB = float(-np.sum(crf.dd[m] * delta) + np.sum(y * crf.dop(m, delta)) + np.sum(delta * crf.dop(m, y)))
+                wbar[m] += abar * (-(dB + 2.0 * alpha * dA) / (2.0 * A))
+            ybar = (1.0 - alpha) * ybar + abar * da_dy
+        else:
+            ybar = (1.0 - alpha) * ybar
+    return phibar, wbar, ybar

@@ -54,6 +54,7 @@ _SIGS = {
     "dcrf_filter_adjoint": ([_P, _P, _I, _P, _I, _P], _I),
     "dcrf_qp_fw": ([_P, _P, _P, _I, _P, _I, _I, _P, _P, _I, _P], _I),
     "dcrf_dc_cccp": ([_P, _P, _P, _I, _P, _I, _I, _I, _P, _P, _I, _P], _I),
+    "dcrf_qp_fw_backward": ([_P, _P, _P, _I, _P, _I, _I, _P, _P, _P, _P, _P, _P], _I),
     "dcrf_lp_subgrad": ([_P, _P, _P, _P, _I, _I, _P, _P, _P], _I),
     "dcrf_lp_solve": ([_P, _P, _P, _I, _I, _I, _D, _P, _P, _P], _I),
     "dcrf_simplex_project": ([_P, _I64, _I, _P, _P], _I),
@@ -227,6 +228,23 @@ def dcrf_qp_fw(unaries: torch.Tensor, lattices, weights, Y: torch.Tensor, iters:
         return None
     arr = np.array([(r.energy, r.gap, r.alpha, r.A, r.B) for r in rec[:iters * batch]], dtype=np.float64)
     return arr.reshape(iters, batch, 5)
+
+
+def dcrf_qp_fw_backward(unaries, lattices, weights, Y0, dYT, iters: int, compat=None, need_dy0: bool = False,
+                        stream=None):
+    """(dphi [N, L], dweights [n_kernels] float64, dY0 or None) of <dYT, y^T>."""
+    unaries = _dev(unaries, torch.float32, "unaries", 2)
+    Y0 = _dev(Y0, torch.float32, "Y0", 2)
+    dYT = _dev(dYT, torch.float32, "dYT", 2)
+    L = unaries.shape[1]
+    dphi = torch.empty_like(unaries)
+    dy0 = torch.empty_like(Y0) if need_dy0 else None
+    dw = np.zeros(len(lattices), dtype=np.float64)
+    cm = _compat(compat, L)
+    _check(lib().dcrf_qp_fw_backward(_ptr(unaries), _handles(lattices), _floats(weights), len(lattices),
+                                     None if cm is None else cm[1], L, iters, _ptr(Y0), _ptr(dYT), _ptr(dphi),
+                                     _ptr(dy0), dw.ctypes.data_as(_P), _stream(stream)), "dcrf_qp_fw_backward")
+    return dphi, dw, dy0
 
 
 def dcrf_dc_cccp(unaries, lattices, weights, Y, outer: int, inner: int, compat=None, storage="f32",

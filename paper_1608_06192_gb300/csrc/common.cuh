@@ -141,3 +141,5 @@ dcrf_status dcrf_splat_dense(const dcrf_lattice lat, const float *Y, int L, floa
 // scratch of the same type as dst.  src is left intact.
 dcrf_status dcrf_blur(const dcrf_lattice lat, const float *src, void *dst, void *tmp, int Lp,
                       int storage, bool reverse, cudaStream_t s);
+// out [n][L] = s0 * slice of float32 lattice values V [m][Lp].
+dcrf_status dcrf_slice_f32(const dcrf_lattice lat, const float *V, int Lp, int L, float *out, cudaStream_t s);

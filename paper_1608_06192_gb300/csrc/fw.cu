@@ -14,6 +14,7 @@
 // <y, P_s> and <s, P_s> use S^T = slice: <u, K~ v> = sum_m w_m s0_m <S u, B S v>
 // is a dot product over lattice vertices.  Each iteration therefore reads the
 // per-pixel state (y, phi - d, s, simplex table) once and writes y and s once.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -21,7 +22,7 @@
 
 namespace {
 
-constexpr int kPixBlock = 128;   // pixels per block (one chunk)
+constexpr int kPixBlock = 256;   // pixels per block (one chunk)
 constexpr int kVertBlock = 128;  // vertices per block
 constexpr int NS = 8;            // per-pixel scalar sums, see k_fw_pixel
 
@@ -96,8 +97,7 @@ __device__ __forceinline__ void block_reduce_add(double (&v)[N], double *acc) {
 //   4: -sum_w <y', mu e_s'> + y'(s') d(s')   (pixel part of <y', (Psi+D) s'>)
 //   5: -sum_w mu(s', s') + d(s')            (pixel part of <s', (Psi+D) s'>)
 //   6: <y', D y'>  7: <phi, y'> (only when phi is given)
-// and S s' is splatted into Slat (warp-aggregated: lanes that hit the same
-// (vertex, label) add their weights in 2^-24 fixed point, one atomic per group).
+// and S s' is splatted into Slat.
 struct PixArgs {
     const Chunk *chunks;
     const double *alpha;   // [batch] or null (start: alpha = 0)
@@ -122,8 +122,48 @@ __device__ __forceinline__ const float *slice_src<float>(const FwLat &lt) { retu
 template <>
 __device__ __forceinline__ const __half *slice_src<__half>(const FwLat &lt) { return lt.BYh; }
 
+// Eight labels of a lattice row: 2 x float4 (float32) or 1 x uint4 (half).
+__device__ __forceinline__ void ld8(const float *p, int64_t row, int LP, int h, float (&o)[8]) {
+    const float4 *q = reinterpret_cast<const float4 *>(p + row * LP + 8 * h);
+    const float4 a = __ldg(q), b = __ldg(q + 1);
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+}
+__device__ __forceinline__ void ld8(const __half *p, int64_t row, int LP, int h, float (&o)[8]) {
+    const uint4 raw = __ldg(reinterpret_cast<const uint4 *>(p + row * LP + 8 * h));
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&raw.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&raw.y));
+    const float2 c = __half22float2(*reinterpret_cast<const __half2 *>(&raw.z));
+    const float2 d = __half22float2(*reinterpret_cast<const __half2 *>(&raw.w));
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y; o[4] = c.x; o[5] = c.y; o[6] = d.x; o[7] = d.y;
+}
+
+// Sum over the block: FP32 within each warp, FP64 across warps and blocks.
+template <int N>
+__device__ __forceinline__ void block_reduce_f32(float (&v)[N], double *acc) {
+    __shared__ double red[32][N];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        float x = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) red[warp][q] = (double)x;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            double x = lane < nw ? red[lane][q] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if (lane == 0) atomicAdd(acc + q, x);
+        }
+    }
+}
+
 template <int LP, typename TB, bool POTTS>
-__global__ void __launch_bounds__(kPixBlock) k_fw_pixel(PixArgs A, FwLats F) {
+__global__ void __launch_bounds__(kPixBlock, 3) k_fw_pixel(PixArgs A, FwLats F) {
     extern __shared__ float smem[];
     float *sy = smem;
     float *sl = smem + kPixBlock * A.Ls;
@@ -131,31 +171,36 @@ __global__ void __launch_bounds__(kPixBlock) k_fw_pixel(PixArgs A, FwLats F) {
     const int L = A.L;
     const int64_t base = ch.begin * (int64_t)L;
     const int cnt = ch.count * L;
-    for (int i = threadIdx.x; i < cnt; i += kPixBlock) {
-        int r = i / L, c = i - r * L;
-        sy[r * A.Ls + c] = A.Y[base + i];
-        sl[r * A.Ls + c] = A.lin[base + i];
+    if (A.Ls == L) {
+        for (int i = threadIdx.x; i < cnt; i += kPixBlock) {
+            sy[i] = A.Y[base + i];
+            sl[i] = A.lin[base + i];
+        }
+    } else {
+        for (int i = threadIdx.x; i < cnt; i += kPixBlock) {
+            int r = i / L, c = i - r * L;
+            sy[r * A.Ls + c] = A.Y[base + i];
+            sl[r * A.Ls + c] = A.lin[base + i];
+        }
     }
     __syncthreads();
     const bool start = A.alpha == nullptr;
     const float al = start ? 0.f : (float)A.alpha[ch.image];
-    double part[NS];
+    float part[NS];
 #pragma unroll
-    for (int q = 0; q < NS; ++q) part[q] = 0.0;
+    for (int q = 0; q < NS; ++q) part[q] = 0.f;
     const int t = threadIdx.x;
     const bool valid = t < ch.count;
     const int64_t a = ch.begin + (valid ? t : 0);
+    const float *yrow = sy + t * A.Ls;
+    const float *lrow = sl + t * A.Ls;
     int sb = 0;
     if (valid) {
-        float y[LP], ky[LP];
-        const int sold = A.s[a];
+        const int sold = start ? -1 : A.s[a];
+        // K~ y' gathered from the lattice, eight labels at a time
+        float ky[LP];
 #pragma unroll
-        for (int i = 0; i < LP; ++i) {
-            float v = i < L ? sy[t * A.Ls + i] : 0.f;
-            if (!start && i < L) v = v + al * ((i == sold ? 1.f : 0.f) - v);
-            y[i] = v;
-            ky[i] = 0.f;
-        }
+        for (int i = 0; i < LP; ++i) ky[i] = 0.f;
 #pragma unroll
         for (int mm = 0; mm < DCRF_MAX_KERNELS; ++mm) {
             if (mm >= F.nk) break;
@@ -166,28 +211,31 @@ __global__ void __launch_bounds__(kPixBlock) k_fw_pixel(PixArgs A, FwLats F) {
                 if (v < 0) continue;
                 const float w = __ldg(lt.pbary + a * lt.d1 + k) * lt.ws0;
 #pragma unroll
-                for (int g = 0; g < LP / 4; ++g) {
-                    const float4 by = ld4(src, (int64_t)v * (LP / 4) + g);
-                    ky[4 * g + 0] += w * by.x;
-                    ky[4 * g + 1] += w * by.y;
-                    ky[4 * g + 2] += w * by.z;
-                    ky[4 * g + 3] += w * by.w;
+                for (int h = 0; h < LP / 8; ++h) {
+                    float o[8];
+                    ld8(src, v, LP, h, o);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) ky[8 * h + j] += w * o[j];
                 }
             }
         }
+        // y' = y + alpha (e_sold - y), read back from shared memory when needed
+        auto yp = [&](int i) {
+            const float v = yrow[i];
+            return start ? v : v + al * ((i == sold ? 1.f : 0.f) - v);
+        };
         const float ca = A.c[a];
-        // X = K~ y' - sum_w y' (in ky);  P = mu X + d o y'
-        float tot = 0.f;
+        float tot = 0.f, sy_ = 0.f;
 #pragma unroll
         for (int i = 0; i < LP; ++i) {
-            ky[i] = i < L ? ky[i] - A.sumw * y[i] : 0.f;
-            tot += ky[i];
+            if (i < L) {
+                const float y = yp(i);
+                ky[i] -= A.sumw * y;          // X = K~ y' - sum_w y'
+                tot += ky[i];
+                sy_ += y;
+            }
         }
-        if (POTTS) {
-            const float dpot = (float)(L - 1) * ca;
-#pragma unroll
-            for (int i = 0; i < LP; ++i) ky[i] = i < L ? (tot - ky[i]) + dpot * y[i] : 0.f;
-        } else {
+        if (!POTTS) {
             float X[LP];
 #pragma unroll
             for (int i = 0; i < LP; ++i) X[i] = ky[i];
@@ -198,29 +246,30 @@ __global__ void __launch_bounds__(kPixBlock) k_fw_pixel(PixArgs A, FwLats F) {
 #pragma unroll
                     for (int j = 0; j < LP; ++j)
                         if (j < L) acc += A.mu[i * L + j] * X[j];
-                    ky[i] = acc + A.musum[i] * ca * y[i];
+                    ky[i] = acc;              // mu X
                 }
             }
         }
-        // ky now holds P = (Psi + D) y'
+        const float dpot = (float)(L - 1) * ca;
         float best = INFINITY;
-        float s0 = 0.f, s1 = 0.f, s6 = 0.f, sy_ = 0.f;
+        float s0 = 0.f, s1 = 0.f, s6 = 0.f;
         float lin_s = 0.f, P_s = 0.f, y_s = 0.f;
 #pragma unroll
         for (int i = 0; i < LP; ++i) {
             if (i < L) {
-                const float li = sl[t * A.Ls + i];
-                const float g = li + 2.f * ky[i];
-                if (g < best) { best = g; sb = i; lin_s = li; P_s = ky[i]; y_s = y[i]; }
-                s0 += li * y[i];
-                s1 += y[i] * ky[i];
-                s6 += (POTTS ? (float)(L - 1) : A.musum[i]) * ca * y[i] * y[i];
-                sy_ += y[i];
+                const float y = yp(i);
+                const float di = POTTS ? dpot : A.musum[i] * ca;
+                const float P = (POTTS ? tot - ky[i] : ky[i]) + di * y;    // (Psi + D) y'
+                const float li = lrow[i];
+                const float g = li + 2.f * P;
+                if (g < best) { best = g; sb = i; lin_s = li; P_s = P; y_s = y; }
+                s0 += li * y;
+                s1 += y * P;
+                s6 += di * y * y;
             }
         }
         if (!(best < INFINITY)) dcrf_flag(A.status, DCRF_E_NONFINITE);
-        float ymu;   // <y', mu e_s'> = sum_i y'_i mu(i, s')
-        float mu_ss;
+        float ymu, mu_ss;   // <y', mu e_s'>, mu(s', s')
         if (POTTS) {
             ymu = sy_ - y_s;
             mu_ss = 0.f;
@@ -228,60 +277,54 @@ __global__ void __launch_bounds__(kPixBlock) k_fw_pixel(PixArgs A, FwLats F) {
             ymu = 0.f;
 #pragma unroll
             for (int i = 0; i < LP; ++i)
-                if (i < L) ymu += y[i] * A.mu[i * L + sb];
+                if (i < L) ymu += yp(i) * A.mu[i * L + sb];
             mu_ss = A.mu[sb * L + sb];
         }
-        const float ds = (POTTS ? (float)(L - 1) : A.musum[sb]) * ca;
+        const float ds = POTTS ? dpot : A.musum[sb] * ca;
         part[0] = s0;
         part[1] = s1;
         part[2] = lin_s;
         part[3] = P_s;
-        part[4] = (double)(-A.sumw * ymu) + (double)y_s * ds;
-        part[5] = (double)(-A.sumw * mu_ss) + ds;
+        part[4] = -A.sumw * ymu + y_s * ds;
+        part[5] = -A.sumw * mu_ss + ds;
         part[6] = s6;
         if (A.phi) {
             float sp = 0.f;
 #pragma unroll
             for (int i = 0; i < LP; ++i)
-                if (i < L) sp += A.phi[a * L + i] * y[i];
+                if (i < L) sp += A.phi[a * L + i] * yp(i);
             part[7] = sp;
         }
+        A.s[a] = (uint8_t)sb;
         if (!start) {
+            float *yw = sy + t * A.Ls;
 #pragma unroll
             for (int i = 0; i < LP; ++i)
-                if (i < L) sy[t * A.Ls + i] = y[i];
+                if (i < L) yw[i] = yp(i);
         }
-        A.s[a] = (uint8_t)sb;
-    }
-    // splat of the one-hot s' (every lane of the block takes part)
+        // splat of the one-hot s' into Slat (FP32 reductions in L2)
 #pragma unroll
-    for (int mm = 0; mm < DCRF_MAX_KERNELS; ++mm) {
-        if (mm >= F.nk) break;
-        const FwLat &lt = F.l[mm];
-        for (int k = 0; k < lt.d1; ++k) {
-            long long key = -1;
-            unsigned u = 0;
-            if (valid) {
+        for (int mm = 0; mm < DCRF_MAX_KERNELS; ++mm) {
+            if (mm >= F.nk) break;
+            const FwLat &lt = F.l[mm];
+            for (int k = 0; k < lt.d1; ++k) {
                 const int v = __ldg(lt.pvid + a * lt.d1 + k);
-                if (v >= 0) {
-                    key = (long long)v * LP + sb;
-                    u = __float2uint_rn(__ldg(lt.pbary + a * lt.d1 + k) * 16777216.f);
-                }
+                if (v >= 0) atomicAdd(lt.Slat + (int64_t)v * LP + sb, __ldg(lt.pbary + a * lt.d1 + k));
             }
-            const unsigned peers = __match_any_sync(0xffffffffu, key);
-            const unsigned sum = __reduce_add_sync(peers, u);
-            if (key >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1)
-                atomicAdd(lt.Slat + key, (float)sum * (1.f / 16777216.f));
         }
     }
     __syncthreads();
     if (!start) {
-        for (int i = threadIdx.x; i < cnt; i += kPixBlock) {
-            int r = i / L, c = i - r * L;
-            A.Y[base + i] = sy[r * A.Ls + c];
+        if (A.Ls == L) {
+            for (int i = threadIdx.x; i < cnt; i += kPixBlock) A.Y[base + i] = sy[i];
+        } else {
+            for (int i = threadIdx.x; i < cnt; i += kPixBlock) {
+                int r = i / L, c = i - r * L;
+                A.Y[base + i] = sy[r * A.Ls + c];
+            }
         }
     }
-    block_reduce_add<NS>(part, A.acc + (int64_t)ch.image * NS);
+    block_reduce_f32<NS>(part, A.acc + (int64_t)ch.image * NS);
 }
 
 // Lattice dot products for the line search:
@@ -747,6 +790,349 @@ extern "C" dcrf_status dcrf_dc_cccp(const float *unaries, const dcrf_lattice *la
     if (qp_energy) {
         DCRF_TRY(cudaMemcpyAsync(qp_energy, qe, (size_t)(outer + 1) * S.batch * sizeof(double),
                                  cudaMemcpyDeviceToHost, s));
+        int h = 0;
+        DCRF_TRY(cudaMemcpyAsync(&h, S.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        DCRF_TRY(cudaStreamSynchronize(s));
+        if (h != 0) return (dcrf_status)h;
+    }
+    return DCRF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Reverse mode through unrolled Frank-Wolfe.
+//
+// With P = Op(y) = (Psi + D) y, one iteration is y+ = y + alpha (s - y) with
+// alpha = -B / (2A) when A > 0 and 0 < alpha < 1 (else alpha is locally
+// constant), s piecewise constant.  With Delta = s - y and
+// u = y + (2 alpha - 1) Delta:
+//   d alpha / d y   = (lin + Op u + Op^T u) / (2A),   d alpha / d phi = -Delta / (2A),
+//   d alpha / d w_m = -(dB_m + 2 alpha dA_m) / (2A),  dA_m = <Delta, Op_m' Delta>,
+//   dB_m = -<d_m', Delta> + <y, Op_m' Delta> + <Delta, Op_m' y>,
+// Op_m' v = mu (K~_m v - v) + d_m' o v,  d_m' = (sum_j |mu_ij|) (K~_m 1 - 1) [c > 0].
+// Reverse step: abar = <ybar, Delta>, ybar <- (1 - alpha) ybar + abar d alpha/dy.
+namespace {
+
+constexpr int NB = 1 + 2 * DCRF_MAX_KERNELS;   // abar, dA_m, dB_m
+
+struct BwArgs {
+    const Chunk *chunks;
+    const float *Yt;                  // [n][L] y^t
+    const uint8_t *st;                // [n] s^t
+    const float *lin;                 // [n][L] phi - d
+    const float *c;                   // [n] clamped c
+    const float *ones[DCRF_MAX_KERNELS];
+    const float *KY[DCRF_MAX_KERNELS];
+    const float *KS[DCRF_MAX_KERNELS];
+    const float *KTu[DCRF_MAX_KERNELS];
+    float w[DCRF_MAX_KERNELS];
+    int nk;
+    const float *mu;
+    const float *musum;
+    float sumw;
+    int L;
+    float *ybar;
+    float *phibar;
+    double *acc;                      // [batch][NB]
+    const float *coef;                // [batch] abar / (2A) when interior, else 0
+    const float *oma;                 // [batch] 1 - alpha
+    const float *tam1;                // [batch] 2 alpha - 1
+};
+
+template <int LP, bool POTTS>
+__device__ __forceinline__ void apply_mu(const float (&x)[LP], float (&out)[LP], const float *mu, int L, bool transpose) {
+    if (POTTS) {
+        float tot = 0.f;
+#pragma unroll
+        for (int i = 0; i < LP; ++i) tot += i < L ? x[i] : 0.f;
+#pragma unroll
+        for (int i = 0; i < LP; ++i) out[i] = i < L ? tot - x[i] : 0.f;
+    } else {
+#pragma unroll
+        for (int i = 0; i < LP; ++i) {
+            float acc = 0.f;
+#pragma unroll
+            for (int j = 0; j < LP; ++j)
+                if (i < L && j < L) acc += (transpose ? mu[j * L + i] : mu[i * L + j]) * x[j];
+            out[i] = acc;
+        }
+    }
+}
+
+__device__ __forceinline__ float active_c(const BwArgs &B, int64_t a) {
+    float s = 0.f, sw = 0.f;
+    for (int m = 0; m < B.nk; ++m) { s += B.w[m] * B.ones[m][a]; sw += B.w[m]; }
+    return s - sw > 0.f ? 1.f : 0.f;
+}
+
+template <int LP, bool POTTS>
+__global__ void __launch_bounds__(128) k_bw_reduce(BwArgs B) {
+    const Chunk ch = B.chunks[blockIdx.x];
+    double part[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) part[q] = 0.0;
+    if ((int)threadIdx.x < ch.count) {
+        const int64_t a = ch.begin + threadIdx.x;
+        const int L = B.L;
+        const int s = B.st[a];
+        float y[LP], dl[LP];
+        float ab = 0.f;
+#pragma unroll
+        for (int i = 0; i < LP; ++i) {
+            y[i] = i < L ? B.Yt[a * L + i] : 0.f;
+            dl[i] = i < L ? (i == s ? 1.f : 0.f) - y[i] : 0.f;
+            if (i < L) ab += B.ybar[a * L + i] * dl[i];
+        }
+        part[0] = ab;
+        const float act = active_c(B, a);
+        for (int m = 0; m < B.nk; ++m) {
+            float xd[LP], xy[LP], md[LP], my[LP];
+            const float dm = (B.ones[m][a] - 1.f) * act;
+#pragma unroll
+            for (int i = 0; i < LP; ++i) {
+                const float ky = i < L ? B.KY[m][a * L + i] : 0.f;
+                const float ks = i < L ? B.KS[m][a * L + i] : 0.f;
+                xd[i] = (ks - ky) - dl[i];
+                xy[i] = ky - y[i];
+            }
+            apply_mu<LP, POTTS>(xd, md, B.mu, L, false);
+            apply_mu<LP, POTTS>(xy, my, B.mu, L, false);
+            float dA = 0.f, dB = 0.f;
+#pragma unroll
+            for (int i = 0; i < LP; ++i) {
+                if (i < L) {
+                    const float ddi = (POTTS ? (float)(L - 1) : B.musum[i]) * dm;
+                    const float opd = md[i] + ddi * dl[i];     // Op_m' Delta
+                    const float opy = my[i] + ddi * y[i];      // Op_m' y
+                    dA += dl[i] * opd;
+                    dB += -ddi * dl[i] + y[i] * opd + dl[i] * opy;
+                }
+            }
+            part[1 + 2 * m] = dA;
+            part[2 + 2 * m] = dB;
+        }
+    }
+    block_reduce_add<NB>(part, B.acc + (int64_t)ch.image * NB);
+}
+
+__global__ void k_bw_coef(int batch, int nk, double *acc, const dcrf_fw_record *rec, int t, float *coef,
+                          float *oma, float *tam1, double *wbar) {
+    if (threadIdx.x != 0) return;
+    for (int b = 0; b < batch; ++b) {
+        const dcrf_fw_record r = rec[(int64_t)t * batch + b];
+        double *g = acc + (int64_t)b * NB;
+        const bool interior = r.A > 0.0 && r.alpha > 0.0 && r.alpha < 1.0;
+        const double abar = g[0];
+        coef[b] = interior ? (float)(abar / (2.0 * r.A)) : 0.f;
+        oma[b] = (float)(1.0 - r.alpha);
+        tam1[b] = (float)(2.0 * r.alpha - 1.0);
+        if (interior)
+            for (int m = 0; m < nk; ++m)
+                wbar[m] += abar * (-(g[2 + 2 * m] + 2.0 * r.alpha * g[1 + 2 * m]) / (2.0 * r.A));
+        for (int q = 0; q < NB; ++q) g[q] = 0.0;
+    }
+}
+
+__global__ void k_bw_dense(const Chunk *chunks, const float *Yt, const uint8_t *st, int L, const float *tam1,
+                           float *S, float *U) {
+    const Chunk ch = chunks[blockIdx.x];
+    if ((int)threadIdx.x >= ch.count) return;
+    const int64_t a = ch.begin + threadIdx.x;
+    const int s = st[a];
+    const float k = tam1[ch.image];
+    for (int i = 0; i < L; ++i) {
+        const float y = Yt[a * L + i];
+        const float e = i == s ? 1.f : 0.f;
+        S[a * L + i] = e;
+        U[a * L + i] = y + k * (e - y);      // u = y + (2 alpha - 1)(s - y)
+    }
+}
+
+template <int LP, bool POTTS>
+__global__ void __launch_bounds__(128) k_bw_update(BwArgs B) {
+    const Chunk ch = B.chunks[blockIdx.x];
+    if ((int)threadIdx.x >= ch.count) return;
+    const int64_t a = ch.begin + threadIdx.x;
+    const int L = B.L;
+    const int s = B.st[a];
+    const float cf = B.coef[ch.image], om = B.oma[ch.image], k = B.tam1[ch.image];
+    const float ca = B.c[a];
+    float y[LP], dl[LP], xy[LP], xd[LP], xu[LP];
+#pragma unroll
+    for (int i = 0; i < LP; ++i) {
+        y[i] = i < L ? B.Yt[a * L + i] : 0.f;
+        dl[i] = i < L ? (i == s ? 1.f : 0.f) - y[i] : 0.f;
+        xy[i] = -B.sumw * y[i];
+        xd[i] = -B.sumw * dl[i];
+        xu[i] = -B.sumw * (y[i] + k * dl[i]);
+    }
+    for (int m = 0; m < B.nk; ++m) {
+#pragma unroll
+        for (int i = 0; i < LP; ++i) {
+            if (i < L) {
+                const float ky = B.KY[m][a * L + i], ks = B.KS[m][a * L + i], kt = B.KTu[m][a * L + i];
+                xy[i] += B.w[m] * ky;
+                xd[i] += B.w[m] * (ks - ky);
+                xu[i] += B.w[m] * kt;
+            }
+        }
+    }
+    float my[LP], md[LP], mu_[LP];
+    apply_mu<LP, POTTS>(xy, my, B.mu, L, false);
+    apply_mu<LP, POTTS>(xd, md, B.mu, L, false);
+    apply_mu<LP, POTTS>(xu, mu_, B.mu, L, true);
+#pragma unroll
+    for (int i = 0; i < LP; ++i) {
+        if (i < L) {
+            const float di = (POTTS ? (float)(L - 1) : B.musum[i]) * ca;
+            const float u = y[i] + k * dl[i];
+            const float opy = my[i] + di * y[i];
+            const float opd = md[i] + di * dl[i];
+            const float opu = opy + k * opd;
+            const float optu = mu_[i] + di * u;
+            const float g = B.ybar[a * L + i];
+            B.ybar[a * L + i] = om * g + cf * (B.lin[a * L + i] + opu + optu);
+            B.phibar[a * L + i] -= cf * dl[i];
+        }
+    }
+}
+
+template <int LP, bool POTTS>
+dcrf_status bw_launch(BwArgs &B, int nchunks, bool reduce, cudaStream_t s) {
+    if (nchunks == 0) return DCRF_OK;
+    if (reduce) k_bw_reduce<LP, POTTS><<<nchunks, 128, 0, s>>>(B);
+    else k_bw_update<LP, POTTS><<<nchunks, 128, 0, s>>>(B);
+    DCRF_LAUNCHED();
+    return DCRF_OK;
+}
+
+dcrf_status bw_dispatch(BwArgs &B, int Lp, bool potts, int nchunks, bool reduce, cudaStream_t s) {
+    if (Lp == 8) return potts ? bw_launch<8, true>(B, nchunks, reduce, s) : bw_launch<8, false>(B, nchunks, reduce, s);
+    if (Lp == 24) return potts ? bw_launch<24, true>(B, nchunks, reduce, s) : bw_launch<24, false>(B, nchunks, reduce, s);
+    return potts ? bw_launch<64, true>(B, nchunks, reduce, s) : bw_launch<64, false>(B, nchunks, reduce, s);
+}
+
+// out = K~ in (or K~^T in) for one lattice, float32 values.
+dcrf_status dense_filter(const dcrf_lattice lat, const float *in, int L, int Lp, float *out, bool adjoint,
+                         float *V, float *dst, float *tmp, cudaStream_t s) {
+    if (lat->n == 0) return DCRF_OK;
+    DCRF_TRY(cudaMemsetAsync(V, 0, (size_t)lat->m * Lp * sizeof(float), s));
+    DCRF_CHECK_STATUS(dcrf_splat_dense(lat, in, L, V, Lp, s));
+    DCRF_CHECK_STATUS(dcrf_blur(lat, V, dst, tmp, Lp, DCRF_STORAGE_F32, adjoint, s));
+    return dcrf_slice_f32(lat, dst, Lp, L, out, s);
+}
+
+}  // namespace
+
+extern "C" dcrf_status dcrf_qp_fw_backward(const float *unaries, const dcrf_lattice *lattices, const float *weights,
+                                           int n_kernels, const float *compat, int L, int iters, const float *Y0,
+                                           const float *dYT, float *dphi, float *dY0, double *dweights,
+                                           dcrf_stream stream) {
+    if (iters < 0 || !Y0 || !dYT || !dphi) return DCRF_E_INVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    Solver S(s);
+    float *Y;
+    DCRF_CHECK_STATUS(dcrf_check_lattices(lattices, n_kernels));
+    const int64_t n = lattices[0]->n;
+    if (L < 1 || L > DCRF_MAX_L) return DCRF_E_INVAL;
+    DCRF_CHECK_STATUS(S.sc.get(&Y, (size_t)(n > 0 ? n : 1) * L));
+    if (n > 0) DCRF_TRY(cudaMemcpyAsync(Y, Y0, n * L * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    DCRF_CHECK_STATUS(S.setup(unaries, lattices, weights, n_kernels, compat, L, DCRF_STORAGE_F32, Y, iters));
+    const int nk = S.nk, Lp = S.Lp, batch = S.batch;
+    double *wbar;
+    DCRF_CHECK_STATUS(S.sc.get(&wbar, (size_t)nk));
+    DCRF_TRY(cudaMemsetAsync(wbar, 0, nk * sizeof(double), s));
+    if (n > 0) DCRF_TRY(cudaMemsetAsync(dphi, 0, n * L * sizeof(float), s));
+    if (n == 0) {
+        if (dweights) for (int m = 0; m < nk; ++m) dweights[m] = 0.0;
+        return DCRF_OK;
+    }
+    // forward recompute with a checkpoint of (y^t, s^t) before every iteration
+    float *ytape;
+    uint8_t *stape;
+    DCRF_CHECK_STATUS(S.sc.get(&ytape, (size_t)(iters > 0 ? iters : 1) * n * L));
+    DCRF_CHECK_STATUS(S.sc.get(&stape, (size_t)(iters > 0 ? iters : 1) * n));
+    DCRF_CHECK_STATUS(S.pixel(Y, nullptr, true));
+    for (int t = 0; t < iters; ++t) {
+        DCRF_TRY(cudaMemcpyAsync(ytape + (int64_t)t * n * L, Y, n * L * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        DCRF_TRY(cudaMemcpyAsync(stape + (int64_t)t * n, S.sidx, n, cudaMemcpyDeviceToDevice, s));
+        DCRF_CHECK_STATUS(S.iterate(Y, nullptr));
+    }
+    // reverse sweep
+    float *ybar, *Sd, *U, *KY[DCRF_MAX_KERNELS], *KS[DCRF_MAX_KERNELS], *KTu[DCRF_MAX_KERNELS];
+    float *coef, *oma, *tam1, *V, *dst, *tmp;
+    double *acc;
+    const size_t nl = (size_t)n * L;
+    DCRF_CHECK_STATUS(S.sc.get(&ybar, nl));
+    DCRF_CHECK_STATUS(S.sc.get(&Sd, nl));
+    DCRF_CHECK_STATUS(S.sc.get(&U, nl));
+    int64_t mmax = 1;
+    for (int m = 0; m < nk; ++m) {
+        DCRF_CHECK_STATUS(S.sc.get(&KY[m], nl));
+        DCRF_CHECK_STATUS(S.sc.get(&KS[m], nl));
+        DCRF_CHECK_STATUS(S.sc.get(&KTu[m], nl));
+        mmax = std::max<int64_t>(mmax, lattices[m]->m);
+    }
+    DCRF_CHECK_STATUS(S.sc.get(&V, (size_t)mmax * Lp));
+    DCRF_CHECK_STATUS(S.sc.get(&dst, (size_t)mmax * Lp));
+    DCRF_CHECK_STATUS(S.sc.get(&tmp, (size_t)mmax * Lp));
+    DCRF_CHECK_STATUS(S.sc.get(&coef, (size_t)batch));
+    DCRF_CHECK_STATUS(S.sc.get(&oma, (size_t)batch));
+    DCRF_CHECK_STATUS(S.sc.get(&tam1, (size_t)batch));
+    DCRF_CHECK_STATUS(S.sc.get(&acc, (size_t)batch * NB));
+    DCRF_TRY(cudaMemsetAsync(acc, 0, batch * NB * sizeof(double), s));
+    DCRF_TRY(cudaMemsetAsync(tam1, 0, batch * sizeof(float), s));
+    DCRF_TRY(cudaMemcpyAsync(ybar, dYT, nl * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    // 128-row chunks for the reverse kernels
+    auto ch = make_chunks(lattices[0]->point_off, 128);
+    Chunk *chd;
+    DCRF_CHECK_STATUS(S.sc.get(&chd, ch.size() > 0 ? ch.size() : 1));
+    DCRF_TRY(cudaMemcpyAsync(chd, ch.data(), ch.size() * sizeof(Chunk), cudaMemcpyHostToDevice, s));
+    const int nch = (int)ch.size();
+    BwArgs B{};
+    B.chunks = chd;
+    B.lin = S.lin;
+    B.c = S.c;
+    B.nk = nk;
+    for (int m = 0; m < nk; ++m) {
+        B.ones[m] = lattices[m]->ones;
+        B.KY[m] = KY[m];
+        B.KS[m] = KS[m];
+        B.KTu[m] = KTu[m];
+        B.w[m] = weights[m];
+    }
+    B.mu = S.mu;
+    B.musum = S.musum;
+    B.sumw = S.sumw;
+    B.L = L;
+    B.ybar = ybar;
+    B.phibar = dphi;
+    B.acc = acc;
+    B.coef = coef;
+    B.oma = oma;
+    B.tam1 = tam1;
+    for (int t = iters - 1; t >= 0; --t) {
+        const float *Yt = ytape + (int64_t)t * n * L;
+        const uint8_t *st = stape + (int64_t)t * n;
+        B.Yt = Yt;
+        B.st = st;
+        k_bw_dense<<<nch, 128, 0, s>>>(chd, Yt, st, L, tam1, Sd, U);   // S only (U recomputed below)
+        DCRF_LAUNCHED();
+        for (int m = 0; m < nk; ++m) {
+            DCRF_CHECK_STATUS(dense_filter(lattices[m], Yt, L, Lp, KY[m], false, V, dst, tmp, s));
+            DCRF_CHECK_STATUS(dense_filter(lattices[m], Sd, L, Lp, KS[m], false, V, dst, tmp, s));
+        }
+        DCRF_CHECK_STATUS(bw_dispatch(B, Lp, S.potts, nch, true, s));
+        k_bw_coef<<<1, 32, 0, s>>>(batch, nk, acc, S.rec, t, coef, oma, tam1, wbar);
+        DCRF_LAUNCHED();
+        k_bw_dense<<<nch, 128, 0, s>>>(chd, Yt, st, L, tam1, Sd, U);   // u with this iteration's alpha
+        DCRF_LAUNCHED();
+        for (int m = 0; m < nk; ++m)
+            DCRF_CHECK_STATUS(dense_filter(lattices[m], U, L, Lp, KTu[m], true, V, dst, tmp, s));
+        DCRF_CHECK_STATUS(bw_dispatch(B, Lp, S.potts, nch, false, s));
+    }
+    if (dY0) DCRF_TRY(cudaMemcpyAsync(dY0, ybar, nl * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    if (dweights) {
+        DCRF_TRY(cudaMemcpyAsync(dweights, wbar, nk * sizeof(double), cudaMemcpyDeviceToHost, s));
         int h = 0;
         DCRF_TRY(cudaMemcpyAsync(&h, S.status, sizeof(int), cudaMemcpyDeviceToHost, s));
         DCRF_TRY(cudaStreamSynchronize(s));

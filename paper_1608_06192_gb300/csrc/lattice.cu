@@ -410,18 +410,27 @@ dcrf_status dcrf_blur(const dcrf_lattice lat, const float *src, void *dst, void 
     return blur_typed<float>(lat, src, (float *)dst, (float *)tmp, Lp, reverse, s);
 }
 
-// Dense splat: V[vertex_k(a)][c] += b_k(a) * Y[a][c].
+// Dense splat: V[vertex_k(a)][c] += b_k(a) * Y[a][c]; one thread per (point,
+// group of four labels), one 16-byte vector reduction per simplex corner.
 __global__ void k_splat_dense(const float *__restrict__ Y, int64_t n, int L, int Lp, int D1,
                               const int32_t *__restrict__ pvid, const float *__restrict__ pbary,
                               float *__restrict__ V) {
-    int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (a >= n) return;
+    const int G = Lp >> 2;
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * G) return;
+    const int64_t a = idx / G;
+    const int g = (int)(idx - a * G);
+    const int c0 = 4 * g;
+    float4 y;
+    y.x = c0 + 0 < L ? Y[a * L + c0 + 0] : 0.f;
+    y.y = c0 + 1 < L ? Y[a * L + c0 + 1] : 0.f;
+    y.z = c0 + 2 < L ? Y[a * L + c0 + 2] : 0.f;
+    y.w = c0 + 3 < L ? Y[a * L + c0 + 3] : 0.f;
     for (int k = 0; k < D1; ++k) {
-        int v = pvid[a * D1 + k];
+        const int v = pvid[a * D1 + k];
         if (v < 0) continue;
-        float w = pbary[a * D1 + k];
-        float *row = V + (int64_t)v * Lp;
-        for (int c = 0; c < L; ++c) atomicAdd(row + c, w * Y[a * L + c]);
+        const float w = pbary[a * D1 + k];
+        atomicAdd(reinterpret_cast<float4 *>(V + (int64_t)v * Lp + c0), make_float4(w * y.x, w * y.y, w * y.z, w * y.w));
     }
 }
 
@@ -429,8 +438,8 @@ dcrf_status dcrf_splat_dense(const dcrf_lattice lat, const float *Y, int L, floa
                              cudaStream_t s) {
     if (lat->n == 0) return DCRF_OK;
     ProfScope ps(P_SPLAT_DENSE, s);
-    k_splat_dense<<<blocks_for(lat->n, 128), 128, 0, s>>>(Y, lat->n, L, Lp, lat->d + 1, lat->pvid,
-                                                          lat->pbary, V);
+    k_splat_dense<<<blocks_for(lat->n * (Lp / 4), 256), 256, 0, s>>>(Y, lat->n, L, Lp, lat->d + 1, lat->pvid,
+                                                                   lat->pbary, V);
     DCRF_LAUNCHED();
     return DCRF_OK;
 }
@@ -457,6 +466,16 @@ __global__ void k_slice(const T *__restrict__ V, int64_t n, int L, int G, int D1
         int c = 4 * g + i;
         if (c < L) out[a * L + c] = s0 * vals[i];
     }
+}
+
+dcrf_status dcrf_slice_f32(const dcrf_lattice lat, const float *V, int Lp, int L, float *out, cudaStream_t s) {
+    if (lat->n == 0) return DCRF_OK;
+    const int G = Lp / 4;
+    ProfScope ps(P_SLICE, s);
+    k_slice<float><<<blocks_for(lat->n * G, 256), 256, 0, s>>>(V, lat->n, L, G, lat->d + 1, lat->pvid, lat->pbary,
+                                                              (float)lat->s0, out);
+    DCRF_LAUNCHED();
+    return DCRF_OK;
 }
 
 static dcrf_status filter_impl(const dcrf_lattice lat, const float *Y, int L, float *out, int storage,
