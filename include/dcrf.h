@@ -30,6 +30,7 @@
 #ifndef DCRF_H
 #define DCRF_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -47,7 +48,8 @@ typedef enum {
     DCRF_E_TABLE_FULL = -4,  /* lattice hash table ran out of slots (bounded probing) */
     DCRF_E_KEY_RANGE = -5,   /* a lattice coordinate does not fit the packed key */
     DCRF_E_TIMEOUT = -6,     /* a bounded device-side wait gave up */
-    DCRF_E_NONFINITE = -7    /* NaN or Inf met in inputs or a reduction */
+    DCRF_E_NONFINITE = -7,   /* NaN or Inf met in inputs or a reduction */
+    DCRF_E_SCRATCH = -8      /* the request does not fit dcrf_filter_static's fixed scratch */
 } dcrf_status;
 
 typedef enum {
@@ -125,6 +127,26 @@ dcrf_status dcrf_lattice_export(dcrf_lattice lat, int32_t *keys, int32_t *point_
  */
 dcrf_status dcrf_filter(dcrf_lattice lat, const float *Y, int L, float *out, int storage,
                         dcrf_stream stream);
+
+/*
+ * dcrf_filter without any device allocation.  No counterpart in the paper:
+ * it exists for callers that cannot allocate device memory when they filter
+ * (for example while capturing a stream under a mode that forbids
+ * allocation, or real-time code with a fixed memory budget).  Same result and
+ * arguments as dcrf_filter; the splat and blur buffers live in one
+ * file-scope device array of dcrf_filter_static_capacity() bytes (16 MiB),
+ * which every GPU that loads the library holds until the process exits.
+ * Requests with lattice vertices * round4(L) * (4 + 2 * value size) bytes
+ * (each part rounded up to 256) above that size return DCRF_E_SCRATCH.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All
+ * calls share the array and it keeps the last call's contents (the splat
+ * buffer is cleared on entry): calls that overlap on the GPU race, so
+ * serialise them.
+ */
+dcrf_status dcrf_filter_static(dcrf_lattice lat, const float *Y, int L, float *out, int storage,
+                               dcrf_stream stream);
+size_t dcrf_filter_static_capacity(void);
 
 /* Adjoint K~^T U: the same chain with the blur axes in reverse order. */
 dcrf_status dcrf_filter_adjoint(dcrf_lattice lat, const float *U, int L, float *out, int storage,

@@ -52,6 +52,8 @@ _SIGS = {
     "dcrf_lattice_export": ([_P, _P, _P, _P, _P, _P], _I),
     "dcrf_filter": ([_P, _P, _I, _P, _I, _P], _I),
     "dcrf_filter_adjoint": ([_P, _P, _I, _P, _I, _P], _I),
+    "dcrf_filter_static": ([_P, _P, _I, _P, _I, _P], _I),
+    "dcrf_filter_static_capacity": ([], ctypes.c_size_t),
     "dcrf_qp_fw": ([_P, _P, _P, _I, _P, _I, _I, _P, _P, _I, _P], _I),
     "dcrf_dc_cccp": ([_P, _P, _P, _I, _P, _I, _I, _I, _P, _P, _I, _P], _I),
     "dcrf_qp_fw_backward": ([_P, _P, _P, _I, _P, _I, _I, _P, _P, _P, _P, _P, _P], _I),
@@ -201,6 +203,15 @@ def dcrf_filter(lat: Lattice, Y: torch.Tensor, storage: str = "f32", stream=None
     out = torch.empty_like(Y) if out is None else _dev(out, torch.float32, "out", 2)
     _check(lib().dcrf_filter(lat.handle, _ptr(Y), Y.shape[1], _ptr(out), STORAGE[storage], _stream(stream)),
            "dcrf_filter")
+    return out
+
+
+def dcrf_filter_static(lat: Lattice, Y: torch.Tensor, storage: str = "f32", stream=None, out=None):
+    """dcrf_filter without device allocation in the library (fixed static scratch)."""
+    Y = _dev(Y, torch.float32, "Y", 2)
+    out = torch.empty_like(Y) if out is None else _dev(out, torch.float32, "out", 2)
+    _check(lib().dcrf_filter_static(lat.handle, _ptr(Y), Y.shape[1], _ptr(out), STORAGE[storage],
+                                    _stream(stream)), "dcrf_filter_static")
     return out
 
 

@@ -30,6 +30,7 @@ extern "C" const char *dcrf_status_string(int status) {
     case DCRF_E_KEY_RANGE: return "lattice coordinate outside the packed key range";
     case DCRF_E_TIMEOUT: return "bounded device wait expired";
     case DCRF_E_NONFINITE: return "non-finite value";
+    case DCRF_E_SCRATCH: return "request exceeds the fixed scratch of dcrf_filter_static";
     default: return "unknown status";
     }
 }
