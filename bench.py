@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--height", type=int, default=375)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-lp", action="store_true")
     return ap.parse_args()
 
 
@@ -178,18 +179,25 @@ class ClockSampler:
 
 
 def algorithmic_bytes(kind, n, L, lat_m, lat_d, storage):
-    """Bytes one Frank-Wolfe iteration must move for a kernel kind (all launches of it)."""
+    """Bytes one Frank-Wolfe iteration must move for a kernel kind (all launches of it).
+
+    Per pixel: y read+write and (phi - d) read (12 L), s read+write and c (6),
+    vertex id + weight per simplex corner (8 (d+1) per lattice).  Per lattice
+    vertex row of Lp labels: the one-hot splat S s in float32 (4),
+    B S s and the sliced B S y in the storage type (esz), Ylat and BY in float32.
+    """
     Lp = 8 if L <= 8 else (24 if L <= 24 else 64)
     esz = 2 if storage == "f16" else 4
+    half_copy = 2 if storage == "f16" else 0
     if kind == "fw_pixel":
         per_px = 12 * L + 6 + sum(8 * (d + 1) for d in lat_d)
-        return n * per_px + sum(m * Lp * (4 + esz + 4) for m in lat_m)
-    if kind == "blur_pass":
-        return sum((d + 1) * (m * Lp * (2 * esz) + 8 * m) + m * Lp * (4 - esz) for m, d in zip(lat_m, lat_d))
+        return n * per_px + sum(m * Lp * (esz + 4) for m in lat_m)
+    if kind == "fw_blur":
+        return sum(m * Lp * (4 + esz) + d * m * Lp * 2 * esz + (d + 1) * 8 * m for m, d in zip(lat_m, lat_d))
     if kind == "fw_latdot":
         return sum(m * Lp * (8 + esz) for m in lat_m)
     if kind == "fw_latupd":
-        return sum(m * Lp * (20 + esz) + 4 * m for m in lat_m)
+        return sum(m * Lp * (24 + esz + half_copy) + 4 * m for m in lat_m)
     return 0
 
 
@@ -268,7 +276,7 @@ def main():
 
         # roofline of the dominant kernel (CUDA events on the launching stream)
         lat_m, lat_d = [lb.m, ls.m], [5, 2]
-        per_iter_launch = {"fw_pixel": 1, "blur_pass": 9, "fw_latdot": 2, "fw_latupd": 2}
+        per_iter_launch = {"fw_pixel": 1, "fw_blur": max(lat_d) + 1, "fw_latdot": 2, "fw_latupd": 2}
         roof = None
         kinds = {}
         for kind, (cnt, ms) in prof.items():
@@ -307,6 +315,25 @@ def main():
         a1.record(stream)
         stream.synchronize()
         plain_fp32 = reps * T / (a0.elapsed_time(a1) / 1000.0)
+
+        # LP subgradient (sort + divide and conquer) on one 500x375 image, L=21
+        lp = None
+        if not args.no_lp:
+            y_lp = torch.from_numpy(S.dirichlet_labels(n1, L, seed=5)).to(dev)
+            D.dcrf_lp_subgrad(phi[:n1], y_lp, [l1b, l1s], wts, energy=False, stream=stream)
+            stream.synchronize()
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            reps_lp = 2
+            for _ in range(reps_lp):
+                D.dcrf_lp_subgrad(phi[:n1], y_lp, [l1b, l1s], wts, energy=False, stream=stream)
+            c1.record(stream)
+            stream.synchronize()
+            lp_ms = c0.elapsed_time(c1) / reps_lp
+            nlev = int(np.ceil(np.log2(n1)))
+            lp = {"workload": "one 500x375 image, L=21, y ~ Dirichlet(0.5), bilateral + spatial lattices",
+                  "ms_per_subgradient": round(lp_ms, 3), "subgradients_per_s": round(1000.0 / lp_ms, 2),
+                  "label_levels_per_s": round(L * nlev * 1000.0 / lp_ms, 1)}
 
         # end to end through the public API from pinned host buffers
         e2e = None
@@ -363,6 +390,7 @@ def main():
                        "l2": "inputs larger than L2 (per-pixel state of the batch is several GB)",
                        "lattice_build_s": round(build_s, 4)},
             "plain_fp32_single_image": {"value": plain_fp32, "unit": UNIT},
+            "lp_subgrad": lp,
             "roofline": roof,
             "kernels": kinds,
             "cpu_baseline": cpu,

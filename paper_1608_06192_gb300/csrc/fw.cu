@@ -16,13 +16,22 @@
 // per-pixel state (y, phi - d, s, simplex table) once and writes y and s once.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cstring>
 
 #include "common.cuh"
 
 namespace {
 
-constexpr int kPixBlock = 256;   // pixels per block (one chunk)
+// Pixel-kernel variants (pixels per block = threads, minimum blocks per SM);
+// the autotuner picks one per (labels, storage, compatibility, size) at first use.
+constexpr int kPixVariants = 4;
+constexpr int kPixPB[kPixVariants] = {256, 256, 128, 128};
+constexpr int kPixMB[kPixVariants] = {4, 3, 8, 6};
 constexpr int kVertBlock = 128;  // vertices per block
 constexpr int NS = 8;            // per-pixel scalar sums, see k_fw_pixel
 
@@ -162,31 +171,63 @@ __device__ __forceinline__ void block_reduce_f32(float (&v)[N], double *acc) {
     }
 }
 
-template <int LP, typename TB, bool POTTS>
-__global__ void __launch_bounds__(kPixBlock, 3) k_fw_pixel(PixArgs A, FwLats F) {
-    extern __shared__ float smem[];
-    float *sy = smem;
-    float *sl = smem + kPixBlock * A.Ls;
-    const Chunk ch = A.chunks[blockIdx.x];
+__device__ __forceinline__ void cp_async4(float *sdst, const float *gsrc) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Issues the asynchronous copies of one chunk's y and lin rows into shared
+// memory (row stride Ls); the (row, column) of element i advance incrementally.
+__device__ __forceinline__ void tile_load_async(const PixArgs &A, const Chunk &ch, float *sy, float *sl) {
     const int L = A.L;
     const int64_t base = ch.begin * (int64_t)L;
     const int cnt = ch.count * L;
     if (A.Ls == L) {
-        for (int i = threadIdx.x; i < cnt; i += kPixBlock) {
-            sy[i] = A.Y[base + i];
-            sl[i] = A.lin[base + i];
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            cp_async4(sy + i, A.Y + base + i);
+            cp_async4(sl + i, A.lin + base + i);
         }
     } else {
-        for (int i = threadIdx.x; i < cnt; i += kPixBlock) {
-            int r = i / L, c = i - r * L;
-            sy[r * A.Ls + c] = A.Y[base + i];
-            sl[r * A.Ls + c] = A.lin[base + i];
+        int r = threadIdx.x / L, c = threadIdx.x - r * L;
+        const int dr = blockDim.x / L, dc = blockDim.x - dr * L;
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            cp_async4(sy + r * A.Ls + c, A.Y + base + i);
+            cp_async4(sl + r * A.Ls + c, A.lin + base + i);
+            r += dr;
+            c += dc;
+            if (c >= L) { c -= L; ++r; }
         }
     }
-    __syncthreads();
+}
+
+__device__ __forceinline__ void tile_store(const PixArgs &A, const Chunk &ch, const float *sy) {
+    const int L = A.L;
+    const int64_t base = ch.begin * (int64_t)L;
+    const int cnt = ch.count * L;
+    if (A.Ls == L) {
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) A.Y[base + i] = sy[i];
+    } else {
+        int r = threadIdx.x / L, c = threadIdx.x - r * L;
+        const int dr = blockDim.x / L, dc = blockDim.x - dr * L;
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            A.Y[base + i] = sy[r * A.Ls + c];
+            r += dr;
+            c += dc;
+            if (c >= L) { c -= L; ++r; }
+        }
+    }
+}
+
+// One chunk: every pixel of it (see the comment above PixArgs).
+template <int LP, typename TB, bool POTTS>
+__device__ __forceinline__ void pixel_chunk(const PixArgs &A, const FwLats &F, const Chunk &ch, float *sy,
+                                            const float *sl, float (&part)[NS]) {
+    const int L = A.L;
     const bool start = A.alpha == nullptr;
     const float al = start ? 0.f : (float)A.alpha[ch.image];
-    float part[NS];
 #pragma unroll
     for (int q = 0; q < NS; ++q) part[q] = 0.f;
     const int t = threadIdx.x;
@@ -243,7 +284,7 @@ __global__ void __launch_bounds__(kPixBlock, 3) k_fw_pixel(PixArgs A, FwLats F) 
             for (int i = 0; i < LP; ++i) {
                 if (i < L) {
                     float acc = 0.f;
-#pragma unroll
+#pragma unroll 8
                     for (int j = 0; j < LP; ++j)
                         if (j < L) acc += A.mu[i * L + j] * X[j];
                     ky[i] = acc;              // mu X
@@ -313,18 +354,114 @@ __global__ void __launch_bounds__(kPixBlock, 3) k_fw_pixel(PixArgs A, FwLats F) 
             }
         }
     }
+}
+
+// One block per chunk: the chunk's y and lin rows are copied to shared memory
+// (cp.async), every pixel is processed, y' is written back coalesced.
+template <int LP, typename TB, bool POTTS, int PB, int MB>
+__global__ void __launch_bounds__(PB, MB) k_fw_pixel(PixArgs A, FwLats F) {
+    extern __shared__ float smem[];
+    float *sy = smem;
+    float *sl = smem + PB * A.Ls;
+    const Chunk ch = A.chunks[blockIdx.x];
+    tile_load_async(A, ch, sy, sl);
+    cp_commit();
+    cp_wait<0>();
     __syncthreads();
-    if (!start) {
-        if (A.Ls == L) {
-            for (int i = threadIdx.x; i < cnt; i += kPixBlock) A.Y[base + i] = sy[i];
-        } else {
-            for (int i = threadIdx.x; i < cnt; i += kPixBlock) {
-                int r = i / L, c = i - r * L;
-                A.Y[base + i] = sy[r * A.Ls + c];
-            }
-        }
-    }
+    float part[NS];
+    pixel_chunk<LP, TB, POTTS>(A, F, ch, sy, sl, part);
+    __syncthreads();
+    if (A.alpha != nullptr) tile_store(A, ch, sy);
     block_reduce_f32<NS>(part, A.acc + (int64_t)ch.image * NS);
+}
+
+// Blur pass `p` of every lattice in one launch (lattice m takes part while
+// p < d_m + 1): out[v] = in[v]/2 + (in[v - w_p] + in[v + w_p])/4 on whole rows
+// of LP labels, one thread per vertex.  Pass 0 reads the float32 splat Slat;
+// the last pass of lattice m lands in BS, earlier ones alternate with tmp.
+template <typename T>
+__device__ __forceinline__ void row_load(const T *p, int64_t v, int LP, int q, float (&o)[8]);
+template <>
+__device__ __forceinline__ void row_load<float>(const float *p, int64_t v, int LP, int q, float (&o)[8]) {
+    const float4 *r = reinterpret_cast<const float4 *>(p + v * LP + 8 * q);
+    const float4 a = r[0], b = r[1];
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+}
+template <>
+__device__ __forceinline__ void row_load<__half>(const __half *p, int64_t v, int LP, int q, float (&o)[8]) {
+    const uint4 raw = *reinterpret_cast<const uint4 *>(p + v * LP + 8 * q);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&raw.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&raw.y));
+    const float2 c = __half22float2(*reinterpret_cast<const __half2 *>(&raw.z));
+    const float2 d = __half22float2(*reinterpret_cast<const __half2 *>(&raw.w));
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y; o[4] = c.x; o[5] = c.y; o[6] = d.x; o[7] = d.y;
+}
+__device__ __forceinline__ void row_store(float *p, int64_t v, int LP, int q, const float (&o)[8]) {
+    float4 *r = reinterpret_cast<float4 *>(p + v * LP + 8 * q);
+    r[0] = make_float4(o[0], o[1], o[2], o[3]);
+    r[1] = make_float4(o[4], o[5], o[6], o[7]);
+}
+__device__ __forceinline__ void row_store(__half *p, int64_t v, int LP, int q, const float (&o)[8]) {
+    __half2 h0 = __floats2half2_rn(o[0], o[1]), h1 = __floats2half2_rn(o[2], o[3]);
+    __half2 h2 = __floats2half2_rn(o[4], o[5]), h3 = __floats2half2_rn(o[6], o[7]);
+    uint4 raw;
+    raw.x = *reinterpret_cast<uint32_t *>(&h0);
+    raw.y = *reinterpret_cast<uint32_t *>(&h1);
+    raw.z = *reinterpret_cast<uint32_t *>(&h2);
+    raw.w = *reinterpret_cast<uint32_t *>(&h3);
+    *reinterpret_cast<uint4 *>(p + v * LP + 8 * q) = raw;
+}
+
+struct BlurLat {
+    const int32_t *nbr;
+    const float *src0;   // Slat (float32) for pass 0
+    void *dst;           // BS
+    void *tmp;
+    int64_t m;
+    int d1;
+};
+struct BlurSet {
+    BlurLat l[DCRF_MAX_KERNELS];
+    int64_t start[DCRF_MAX_KERNELS + 1];   // prefix of the vertex counts that take part
+    int nk;
+};
+
+template <int LP, typename T>
+__global__ void __launch_bounds__(256) k_fw_blur(BlurSet B, int p) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int mm = 0;
+#pragma unroll
+    for (int k = 1; k < DCRF_MAX_KERNELS; ++k)
+        if (k < B.nk && g >= B.start[k]) mm = k;
+    if (g >= B.start[B.nk]) return;
+    BlurLat lt = B.l[0];
+#pragma unroll
+    for (int k = 1; k < DCRF_MAX_KERNELS; ++k)
+        if (k == mm) lt = B.l[k];
+    if (p >= lt.d1) return;
+    const int64_t v = g - B.start[mm];
+    const int D = lt.d1 - 1;
+    T *out = ((D - p) % 2 == 0) ? (T *)lt.dst : (T *)lt.tmp;
+    const int2 nb = reinterpret_cast<const int2 *>(lt.nbr)[v * lt.d1 + p];
+#pragma unroll
+    for (int q = 0; q < LP / 8; ++q) {
+        float c[8], a[8], b[8];
+        if (p == 0) {
+            row_load<float>(lt.src0, v, LP, q, c);
+            if (nb.x >= 0) row_load<float>(lt.src0, nb.x, LP, q, a);
+            if (nb.y >= 0) row_load<float>(lt.src0, nb.y, LP, q, b);
+        } else {
+            const T *in = ((D - p + 1) % 2 == 0) ? (const T *)lt.dst : (const T *)lt.tmp;
+            row_load<T>(in, v, LP, q, c);
+            if (nb.x >= 0) row_load<T>(in, nb.x, LP, q, a);
+            if (nb.y >= 0) row_load<T>(in, nb.y, LP, q, b);
+        }
+        float o[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            o[j] = 0.5f * c[j] + (nb.x >= 0 ? 0.25f * a[j] : 0.f) + (nb.y >= 0 ? 0.25f * b[j] : 0.f);
+        row_store(out, v, LP, q, o);
+    }
 }
 
 // Lattice dot products for the line search:
@@ -481,8 +618,9 @@ struct Solver {
     float sumw = 0.f;
     const dcrf_lattice *lats = nullptr;
     FwLats F{};
-    Chunk *pix_chunks = nullptr;
-    int n_pix_chunks = 0;
+    Chunk *chunks_pb[2] = {nullptr, nullptr};   // 256- and 128-pixel chunk lists
+    int n_chunks_pb[2] = {0, 0};
+    int variant = -1;                          // chosen pixel-kernel variant
     std::vector<Chunk *> vchunks;
     std::vector<int> n_vchunks;
     float *mu = nullptr, *musum = nullptr, *c = nullptr, *lin = nullptr;
@@ -564,11 +702,13 @@ struct Solver {
             vchunks.push_back(chd);
             n_vchunks.push_back((int)ch.size());
         }
-        auto pc = make_chunks(lattices[0]->point_off, kPixBlock);
-        n_pix_chunks = (int)pc.size();
-        DCRF_CHECK_STATUS(sc.get(&pix_chunks, pc.size() > 0 ? pc.size() : 1));
-        if (!pc.empty())
-            DCRF_TRY(cudaMemcpyAsync(pix_chunks, pc.data(), pc.size() * sizeof(Chunk), cudaMemcpyHostToDevice, s));
+        for (int q = 0; q < 2; ++q) {
+            auto pc = make_chunks(lattices[0]->point_off, q == 0 ? 256 : 128);
+            n_chunks_pb[q] = (int)pc.size();
+            DCRF_CHECK_STATUS(sc.get(&chunks_pb[q], pc.size() > 0 ? pc.size() : 1));
+            if (!pc.empty())
+                DCRF_TRY(cudaMemcpyAsync(chunks_pb[q], pc.data(), pc.size() * sizeof(Chunk), cudaMemcpyHostToDevice, s));
+        }
         DCRF_CHECK_STATUS(sc.get(&c, (size_t)(n > 0 ? n : 1)));
         DCRF_CHECK_STATUS(sc.get(&lin, (size_t)(n > 0 ? n : 1) * L));
         DCRF_CHECK_STATUS(sc.get(&sidx, (size_t)(n > 0 ? n : 1)));
@@ -599,9 +739,10 @@ struct Solver {
         for (int m = 0; m < nk; ++m) {
             FwLat &l = F.l[m];
             DCRF_CHECK_STATUS(dcrf_splat_dense(lattices[m], Y, L, l.Ylat, Lp, s));
+            // the splat buffer serves as float32 blur scratch, then is cleared
             DCRF_CHECK_STATUS(dcrf_blur(lattices[m], l.Ylat, l.BY, l.Slat, Lp, DCRF_STORAGE_F32, false, s));
             const size_t cnt = (size_t)(l.m > 0 ? l.m : 1) * Lp;
-            DCRF_TRY(cudaMemsetAsync(l.Slat, 0, cnt * sizeof(float), s));   // served as blur scratch
+            DCRF_TRY(cudaMemsetAsync(l.Slat, 0, cnt * sizeof(float), s));
             if (l.BYh && l.m > 0) {
                 k_fw_to_half<<<nblocks(l.m * Lp / 4, 256), 256, 0, s>>>(l.BY, l.BYh, l.m * Lp / 4);
                 DCRF_LAUNCHED();
@@ -610,11 +751,12 @@ struct Solver {
         return DCRF_OK;
     }
 
-    template <int LPc, typename T, bool POT>
-    dcrf_status pixel_t(float *Y, const float *phi, bool start) {
+    template <int LPc, typename T, bool POT, int PB, int MB>
+    dcrf_status pixel_v(float *Y, const float *phi, bool start, const double *alpha_override = nullptr) {
         PixArgs A;
-        A.chunks = pix_chunks;
-        A.alpha = start ? nullptr : alpha;
+        const int q = PB == 256 ? 0 : 1;
+        A.chunks = chunks_pb[q];
+        A.alpha = start ? nullptr : (alpha_override ? alpha_override : alpha);
         A.Y = Y;
         A.lin = lin;
         A.phi = phi;
@@ -627,15 +769,94 @@ struct Solver {
         A.Ls = Ls;
         A.acc = acc;
         A.status = status;
-        const size_t shm = 2 * kPixBlock * Ls * sizeof(float);
-        auto kern = k_fw_pixel<LPc, T, POT>;
-        if (shm > 48 * 1024) DCRF_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-        if (n_pix_chunks > 0) {
+        const size_t shm = 2 * (size_t)PB * Ls * sizeof(float);
+        auto kern = k_fw_pixel<LPc, T, POT, PB, MB>;
+        static bool attr = false;
+        if (!attr) {
+            DCRF_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+            attr = true;
+        }
+        if (n_chunks_pb[q] > 0) {
             ProfScope ps(P_FW_PIXEL, s);
-            kern<<<n_pix_chunks, kPixBlock, shm, s>>>(A, F);
+            kern<<<n_chunks_pb[q], PB, shm, s>>>(A, F);
             DCRF_LAUNCHED();
         }
         return DCRF_OK;
+    }
+
+    // Only the common case (up to 24 labels, Potts) is compiled in every
+    // variant; the others use the first one.
+    template <int LPc, typename T, bool POT>
+    dcrf_status pixel_var(int v, float *Y, const float *phi, bool start, const double *al = nullptr) {
+        if constexpr (LPc == 24 && POT) {
+            switch (v) {
+            case 0: return pixel_v<LPc, T, POT, kPixPB[0], kPixMB[0]>(Y, phi, start, al);
+            case 1: return pixel_v<LPc, T, POT, kPixPB[1], kPixMB[1]>(Y, phi, start, al);
+            case 2: return pixel_v<LPc, T, POT, kPixPB[2], kPixMB[2]>(Y, phi, start, al);
+            default: return pixel_v<LPc, T, POT, kPixPB[3], kPixMB[3]>(Y, phi, start, al);
+            }
+        } else {
+            (void)v;
+            return pixel_v<LPc, T, POT, kPixPB[0], (LPc <= 24 ? kPixMB[0] : 2)>(Y, phi, start, al);
+        }
+    }
+
+    // Autotuner: times every variant on this problem as a full iteration with
+    // a zero step (y' = y exactly, so y is rewritten unchanged; s, the splat
+    // and the scalar sums are reset afterwards) and keeps the fastest per
+    // (Lp, storage, Potts, size bucket).
+    template <int LPc, typename T, bool POT>
+    dcrf_status tune(const float *Y) {
+        static std::mutex mu_;
+        static std::map<std::tuple<int, int, bool, int>, int> cache;
+        int bucket = 0;
+        while ((int64_t)1 << (bucket + 1) <= n) ++bucket;
+        const auto key = std::make_tuple(LPc, storage, POT, bucket);
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            auto it = cache.find(key);
+            if (it != cache.end()) { variant = it->second; return DCRF_OK; }
+        }
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        DCRF_TRY(cudaStreamIsCapturing(s, &cs));
+        if (cs != cudaStreamCaptureStatusNone || n < 4096 || !(LPc == 24 && POT)) { variant = 0; return DCRF_OK; }
+        double *zero = nullptr;
+        DCRF_CHECK_STATUS(sc.get(&zero, (size_t)batch));
+        DCRF_TRY(cudaMemsetAsync(zero, 0, batch * sizeof(double), s));
+        cudaEvent_t e0, e1;
+        DCRF_TRY(cudaEventCreate(&e0));
+        DCRF_TRY(cudaEventCreate(&e1));
+        float best = 1e30f;
+        int arg = 0;
+        float *Yw = const_cast<float *>(Y);
+        for (int v = 0; v < kPixVariants; ++v) {
+            DCRF_CHECK_STATUS((pixel_var<LPc, T, POT>(v, Yw, nullptr, false, zero)));   // warm-up
+            DCRF_TRY(cudaEventRecord(e0, s));
+            for (int r = 0; r < 3; ++r) DCRF_CHECK_STATUS((pixel_var<LPc, T, POT>(v, Yw, nullptr, false, zero)));
+            DCRF_TRY(cudaEventRecord(e1, s));
+            DCRF_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            DCRF_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            if (std::getenv("DCRF_TUNE_LOG"))
+                std::fprintf(stderr, "dcrf tune: Lp=%d storage=%d n=%lld variant %d: %.1f us\n", LPc, storage,
+                             (long long)n, v, 1000.f * ms / 3.f);
+            if (ms < best) { best = ms; arg = v; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        for (int m = 0; m < nk; ++m)
+            DCRF_TRY(cudaMemsetAsync(F.l[m].Slat, 0, (size_t)(F.l[m].m > 0 ? F.l[m].m : 1) * Lp * sizeof(float), s));
+        DCRF_TRY(cudaMemsetAsync(acc, 0, batch * NS * sizeof(double), s));
+        variant = arg;
+        std::lock_guard<std::mutex> lk(mu_);
+        cache[key] = arg;
+        return DCRF_OK;
+    }
+
+    template <int LPc, typename T, bool POT>
+    dcrf_status pixel_t(float *Y, const float *phi, bool start) {
+        if (variant < 0) DCRF_CHECK_STATUS((tune<LPc, T, POT>(Y)));
+        return pixel_var<LPc, T, POT>(variant, Y, phi, start);
     }
 
     template <typename T, bool POT>
@@ -649,6 +870,51 @@ struct Solver {
         if (storage == DCRF_STORAGE_F16)
             return potts ? pixel_lp<__half, true>(Y, phi, start) : pixel_lp<__half, false>(Y, phi, start);
         return potts ? pixel_lp<float, true>(Y, phi, start) : pixel_lp<float, false>(Y, phi, start);
+    }
+
+    // d+1 Jacobi passes of Slat into BS for every lattice, one launch per pass.
+    template <int LPc, typename T>
+    dcrf_status blur_t() {
+        BlurSet B{};
+        B.nk = nk;
+        // lattices in order of decreasing d+1, so the ones still blurring at
+        // pass p are a prefix of the vertex range
+        int order[DCRF_MAX_KERNELS];
+        for (int m = 0; m < nk; ++m) order[m] = m;
+        std::sort(order, order + nk, [&](int a, int b) { return F.l[a].d1 > F.l[b].d1; });
+        B.start[0] = 0;
+        for (int k = 0; k < nk; ++k) {
+            const int m = order[k];
+            B.l[k].nbr = lats[m]->nbr;
+            B.l[k].src0 = F.l[m].Slat;
+            B.l[k].dst = F.l[m].BS;
+            B.l[k].tmp = F.l[m].tmp;
+            B.l[k].m = F.l[m].m;
+            B.l[k].d1 = F.l[m].d1;
+            B.start[k + 1] = B.start[k] + F.l[m].m;
+        }
+        const int dmax = nk > 0 ? B.l[0].d1 : 0;
+        for (int p = 0; p < dmax; ++p) {
+            int active = 0;
+            while (active < nk && B.l[active].d1 > p) ++active;
+            const int64_t work = B.start[active];
+            if (work == 0) continue;
+            ProfScope ps(P_FW_BLUR, s);
+            k_fw_blur<LPc, T><<<nblocks(work, 256), 256, 0, s>>>(B, p);
+            DCRF_LAUNCHED();
+        }
+        return DCRF_OK;
+    }
+
+    dcrf_status blur_all() {
+        if (storage == DCRF_STORAGE_F16) {
+            if (Lp == 8) return blur_t<8, __half>();
+            if (Lp == 24) return blur_t<24, __half>();
+            return blur_t<64, __half>();
+        }
+        if (Lp == 8) return blur_t<8, float>();
+        if (Lp == 24) return blur_t<24, float>();
+        return blur_t<64, float>();
     }
 
     template <int LPc, typename T, bool POT>
@@ -682,8 +948,7 @@ struct Solver {
 
     // One Frank-Wolfe iteration, state at (y, s, Slat = S s, BY = B S y).
     dcrf_status iterate(float *Y, const float *phi) {
-        for (int m = 0; m < nk; ++m)
-            DCRF_CHECK_STATUS(dcrf_blur(lats[m], F.l[m].Slat, F.l[m].BS, F.l[m].tmp, Lp, storage, false, s));
+        DCRF_CHECK_STATUS(blur_all());
         for (int m = 0; m < nk; ++m) DCRF_CHECK_STATUS(latdot(m));
         {
             ProfScope ps(P_FW_ALPHA, s);
@@ -850,7 +1115,7 @@ __device__ __forceinline__ void apply_mu(const float (&x)[LP], float (&out)[LP],
 #pragma unroll
         for (int i = 0; i < LP; ++i) {
             float acc = 0.f;
-#pragma unroll
+#pragma unroll 8
             for (int j = 0; j < LP; ++j)
                 if (i < L && j < L) acc += (transpose ? mu[j * L + i] : mu[i * L + j]) * x[j];
             out[i] = acc;

@@ -114,14 +114,16 @@ struct LevelArgs {
     const int32_t *nlev;      // [batch] levels per image
     const int64_t *csr;       // [m+1] incidence offsets of every vertex (label-independent)
     const int32_t *nbr;       // [m][d1][2]
+    const int32_t *local_from;  // [batch] first level handled by the shared-memory path
     int64_t E, n, m;
     int d1, level;
 };
 
 __device__ __forceinline__ bool entry_node(const LevelArgs &A, int64_t e, int32_t &node, int &bit) {
     const int v = A.vid_s[e];
-    const int B = A.nlev[A.vimg[v]];
-    if (A.level >= B) return false;
+    const int img = A.vimg[v];
+    const int B = A.nlev[img];
+    if (A.level >= B || A.level >= A.local_from[img]) return false;
     const int r = A.rank_s[e];
     node = r >> (B - A.level);
     bit = (r >> (B - A.level - 1)) & 1;
@@ -319,6 +321,168 @@ dcrf_status launch_project(const float *V, int64_t n, int L, const float *G, con
     return DCRF_OK;
 }
 
+// Deep levels in shared memory.  Once a node has at most kLocalP points, one
+// block takes kLocalP consecutive positions of one (label, image): whole nodes.
+// Its tagged vertices (node, vertex) go into a shared-memory hash table, the
+// right-child indicator is splatted, the d+1 Jacobi passes run between two
+// shared arrays, and the left-child points slice their sums into U.
+constexpr int kLocalP = 256;            // positions per block
+constexpr int kLocalSlots = 2048;       // hash slots (load <= 0.75 for d+1 <= 6)
+constexpr int kLocalThreads = 128;
+constexpr uint32_t kLocalEmpty = 0xFFFFFFFFu;
+constexpr int kLocalVertBits = 21;      // local vertex ids below 2^21
+
+struct LocalBlock {
+    int32_t label, image;
+    int32_t p0;        // first position (rank) of the block within the image
+};
+
+struct LocalArgs {
+    const LocalBlock *blocks;
+    const int32_t *perm;          // [L][n]
+    const int32_t *pvid;          // [n][d1]
+    const float *pbary;
+    const int32_t *nbr;           // [m][d1][2]
+    const int64_t *point_off;     // [batch+1]
+    const int64_t *vert_off;      // [batch+1]
+    const int32_t *nlev;          // [batch]
+    float *U;                     // [L][n] by position
+    int64_t n;
+    int d1, level;
+    float ws0;
+};
+
+__device__ __forceinline__ uint32_t local_hash(uint32_t k) { return (k * 0x9E3779B1u) >> (32 - 11); }
+
+__device__ __forceinline__ int local_insert(uint32_t *hkey, uint32_t key) {
+    uint32_t h = local_hash(key);
+    for (int probe = 0; probe < kLocalSlots; ++probe) {
+        const int slot = (int)((h + probe) & (kLocalSlots - 1));
+        const uint32_t prev = atomicCAS(hkey + slot, kLocalEmpty, key);
+        if (prev == kLocalEmpty || prev == key) return slot;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ int local_find(const uint32_t *hkey, uint32_t key) {
+    uint32_t h = local_hash(key);
+    for (int probe = 0; probe < kLocalSlots; ++probe) {
+        const int slot = (int)((h + probe) & (kLocalSlots - 1));
+        const uint32_t cur = hkey[slot];
+        if (cur == key) return slot;
+        if (cur == kLocalEmpty) return -1;
+    }
+    return -1;
+}
+
+__global__ void __launch_bounds__(kLocalThreads) k_lp_local(LocalArgs A) {
+    extern __shared__ uint32_t lsm[];
+    uint32_t *hkey = lsm;
+    float *val = reinterpret_cast<float *>(lsm + kLocalSlots);
+    float *tmp = val + kLocalSlots;
+    const LocalBlock blk = A.blocks[blockIdx.x];
+    const int b = blk.image;
+    const int64_t off = A.point_off[b];
+    const int64_t nb_pts = A.point_off[b + 1] - off;
+    const int64_t voff = A.vert_off[b];
+    const int sh = A.nlev[b] - A.level;          // node = rank >> sh
+    const int p_end = (int)((int64_t)blk.p0 + kLocalP < nb_pts ? (int64_t)blk.p0 + kLocalP : nb_pts);
+    const int node0 = blk.p0 >> sh;
+    const int32_t *perm = A.perm + (int64_t)blk.label * A.n + off;
+    for (int i = threadIdx.x; i < kLocalSlots; i += kLocalThreads) {
+        hkey[i] = kLocalEmpty;
+        val[i] = 0.f;
+    }
+    __syncthreads();
+    // insert every (node, corner vertex); splat the right child's indicator.
+    // Eight entries per thread per step: their global loads are issued first.
+    const int count = (p_end - blk.p0) * A.d1;
+    constexpr int kB = 8;
+    for (int q0 = threadIdx.x; q0 < count; q0 += kB * kLocalThreads) {
+        int vv[kB];
+        float ww[kB];
+        int pp[kB];
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            const int q = q0 + u * kLocalThreads;
+            vv[u] = -1;
+            if (q < count) {
+                const int p = blk.p0 + q / A.d1;
+                const int k = q - (q / A.d1) * A.d1;
+                const int a = perm[p];
+                pp[u] = p;
+                vv[u] = A.pvid[(int64_t)a * A.d1 + k];
+                ww[u] = A.pbary[(int64_t)a * A.d1 + k];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            if (vv[u] < 0) continue;
+            const int p = pp[u];
+            const uint32_t key = ((uint32_t)((p >> sh) - node0) << kLocalVertBits) | (uint32_t)(vv[u] - voff);
+            const int slot = local_insert(hkey, key);
+            if (slot >= 0 && ((p >> (sh - 1)) & 1)) atomicAdd(val + slot, ww[u]);
+        }
+    }
+    __syncthreads();
+    // d+1 Jacobi passes along w_j, absent neighbours read as 0; eight slots per
+    // thread per step so that their neighbour-table loads are in flight together
+    for (int j = 0; j < A.d1; ++j) {
+        for (int s0 = threadIdx.x; s0 < kLocalSlots; s0 += kB * kLocalThreads) {
+            uint32_t kk[kB];
+            int2 nbv[kB];
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                const int slot = s0 + u * kLocalThreads;
+                kk[u] = slot < kLocalSlots ? hkey[slot] : kLocalEmpty;
+                nbv[u] = make_int2(-1, -1);
+                if (kk[u] != kLocalEmpty) {
+                    const int64_t v = voff + (kk[u] & ((1u << kLocalVertBits) - 1));
+                    nbv[u] = reinterpret_cast<const int2 *>(A.nbr)[v * A.d1 + j];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                const int slot = s0 + u * kLocalThreads;
+                if (slot >= kLocalSlots) continue;
+                float r = 0.f;
+                if (kk[u] != kLocalEmpty) {
+                    const uint32_t nodebits = kk[u] & ~((1u << kLocalVertBits) - 1);
+                    r = 0.5f * val[slot];
+                    if (nbv[u].x >= 0) {
+                        const int s2 = local_find(hkey, nodebits | (uint32_t)(nbv[u].x - voff));
+                        if (s2 >= 0) r += 0.25f * val[s2];
+                    }
+                    if (nbv[u].y >= 0) {
+                        const int s2 = local_find(hkey, nodebits | (uint32_t)(nbv[u].y - voff));
+                        if (s2 >= 0) r += 0.25f * val[s2];
+                    }
+                }
+                tmp[slot] = r;
+            }
+        }
+        __syncthreads();
+        float *t = val;
+        val = tmp;
+        tmp = t;
+    }
+    // slice at the left child's points
+    float *U = A.U + (int64_t)blk.label * A.n + off;
+    for (int p = blk.p0 + threadIdx.x; p < p_end; p += kLocalThreads) {
+        if ((p >> (sh - 1)) & 1) continue;
+        const int a = perm[p];
+        const uint32_t lnode = (uint32_t)((p >> sh) - node0);
+        float acc = 0.f;
+        for (int k = 0; k < A.d1; ++k) {
+            const int v = A.pvid[(int64_t)a * A.d1 + k];
+            if (v < 0) continue;
+            const int slot = local_find(hkey, (lnode << kLocalVertBits) | (uint32_t)(v - voff));
+            if (slot >= 0) acc += A.pbary[(int64_t)a * A.d1 + k] * val[slot];
+        }
+        U[p] += A.ws0 * acc;
+    }
+}
+
 // Reusable workspace of the subgradient for one set of lattices.
 struct LpWork {
     cudaStream_t s;
@@ -330,6 +494,11 @@ struct LpWork {
     float ws0[DCRF_MAX_KERNELS];
     int64_t *off_d = nullptr, *seg_b = nullptr, *seg_e = nullptr;
     int32_t *nlev_d = nullptr;
+    int32_t *local_from_d[DCRF_MAX_KERNELS] = {};
+    std::vector<int32_t> nlev_h;
+    std::vector<std::vector<int32_t>> local_from_h;
+    LocalBlock *lblocks = nullptr;
+    size_t lblocks_cap = 0;
     int maxlev = 0;
     float *c = nullptr;
     float *keys = nullptr, *keys2 = nullptr;
@@ -374,6 +543,28 @@ struct LpWork {
         DCRF_TRY(cudaMemcpyAsync(off_d, lattices[0]->point_off.data(), (batch + 1) * sizeof(int64_t),
                                  cudaMemcpyHostToDevice, s));
         DCRF_TRY(cudaMemcpyAsync(nlev_d, nlev.data(), batch * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        nlev_h = nlev;
+        // per lattice and image: the first level whose nodes fit one shared-memory block
+        int pbits = 0;
+        while ((1 << pbits) < kLocalP) ++pbits;
+        local_from_h.assign(nk, std::vector<int32_t>(batch));
+        size_t max_blocks = 1;
+        for (int m = 0; m < nk; ++m) {
+            for (int b = 0; b < batch; ++b) {
+                const int64_t mb = lattices[m]->vert_off[b + 1] - lattices[m]->vert_off[b];
+                const bool ok = lattices[m]->d + 1 <= 6 && mb < (1ll << kLocalVertBits);
+                local_from_h[m][b] = ok ? std::max(0, nlev[b] - pbits) : nlev[b];
+            }
+            DCRF_CHECK_STATUS(sc.get(&local_from_d[m], (size_t)batch));
+            DCRF_TRY(cudaMemcpyAsync(local_from_d[m], local_from_h[m].data(), batch * sizeof(int32_t),
+                                     cudaMemcpyHostToDevice, s));
+        }
+        for (int b = 0; b < batch; ++b) {
+            const int64_t nb_ = lattices[0]->point_off[b + 1] - lattices[0]->point_off[b];
+            max_blocks += (size_t)L * (size_t)((nb_ + kLocalP - 1) / kLocalP);
+        }
+        DCRF_CHECK_STATUS(sc.get(&lblocks, max_blocks));
+        lblocks_cap = max_blocks;
         k_lp_segments<<<nb(L * batch, 128), 128, 0, s>>>(off_d, batch, L, n, seg_b, seg_e);
         DCRF_LAUNCHED();
         const size_t nl = (size_t)(n > 0 ? n : 1) * L;
@@ -490,8 +681,51 @@ struct LpWork {
             A.n = n;
             A.m = m;
             A.d1 = d1;
+            A.local_from = local_from_d[mm];
             for (int lev = 0; lev < maxlev; ++lev) {
                 A.level = lev;
+                // images whose nodes fit a shared-memory block at this level
+                std::vector<LocalBlock> lb;
+                bool any_global = false;
+                for (int b = 0; b < batch; ++b) {
+                    if (lev >= nlev_h[b]) continue;
+                    if (lev >= local_from_h[mm][b]) {
+                        const int64_t nb_ = lat->point_off[b + 1] - lat->point_off[b];
+                        for (int i = 0; i < L; ++i)
+                            for (int64_t p0 = 0; p0 < nb_; p0 += kLocalP) lb.push_back(LocalBlock{i, b, (int32_t)p0});
+                    } else {
+                        any_global = true;
+                    }
+                }
+                if (!lb.empty()) {
+                    DCRF_TRY(cudaMemcpyAsync(lblocks, lb.data(), lb.size() * sizeof(LocalBlock), cudaMemcpyHostToDevice, s));
+                    LocalArgs la;
+                    la.blocks = lblocks;
+                    la.perm = perm;
+                    la.pvid = lat->pvid;
+                    la.pbary = lat->pbary;
+                    la.nbr = lat->nbr;
+                    la.point_off = off_d;
+                    la.vert_off = lat->vert_off_d;
+                    la.nlev = nlev_d;
+                    la.U = U;
+                    la.n = n;
+                    la.d1 = d1;
+                    la.level = lev;
+                    la.ws0 = ws0[mm];
+                    const size_t shm = (size_t)kLocalSlots * 12;
+                    static bool attr = false;
+                    if (!attr) {
+                        DCRF_TRY(cudaFuncSetAttribute(k_lp_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+                        attr = true;
+                    }
+                    ProfScope ps(P_LP_LOCAL, s);
+                    k_lp_local<<<(unsigned)lb.size(), kLocalThreads, shm, s>>>(la);
+                    DCRF_LAUNCHED();
+                    // the block list is read by the kernel before the next level's copy:
+                    // copies and kernels on one stream run in order
+                }
+                if (!any_global) continue;
                 {
                     ProfScope ps(P_LP_RUNS, s);
                     k_lp_flags<<<nb(E, 256), 256, 0, s>>>(A, flag);

@@ -74,3 +74,21 @@ def test_lp_solve_small(dcrf):
     np.testing.assert_allclose(Yg.sum(1), 1.0, atol=1e-5)
     Gb = _oracle_subgrad(p, Yg)
     assert abs(lp.s_lp_from_g(Yg.astype(np.float64), Gb) - e.min()) <= 1e-3 * scale
+
+
+def test_lp_solve_headline_200_steps(dcrf):
+    # 200 projected-subgradient steps at 500x375, L=21 (no oracle at this size:
+    # the iterate stays on the simplex, every energy is finite, the best
+    # energy does not exceed the start and the returned y has that energy)
+    p = S.voc_shaped()
+    g = gpu_setup(dcrf, [p], torch)
+    y0 = S.dirichlet_labels(p.n_pixels, 21, seed=11)
+    Y = torch.from_numpy(y0).cuda()
+    e = dcrf.dcrf_lp_solve(g["phi"], [g["lb"], g["ls"]], p.weights, Y, 200)[:, 0]
+    assert np.isfinite(e).all()
+    assert e.min() <= e[0]
+    Yg = Y.cpu().numpy()
+    np.testing.assert_allclose(Yg.sum(1), 1.0, atol=1e-5)
+    assert Yg.min() >= 0.0
+    _, e_best = dcrf.dcrf_lp_subgrad(g["phi"], Y, [g["lb"], g["ls"]], p.weights)
+    assert abs(e_best[0] - e.min()) <= 1e-3 * abs(e.min())
