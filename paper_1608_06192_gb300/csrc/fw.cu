@@ -807,6 +807,11 @@ struct Solver {
     // (Lp, storage, Potts, size bucket).
     template <int LPc, typename T, bool POT>
     dcrf_status tune(const float *Y) {
+        if (const char *force = std::getenv("DCRF_PIXEL_VARIANT")) {   // testing hook
+            const int v = std::atoi(force);
+            variant = (LPc == 24 && POT && v >= 0 && v < kPixVariants) ? v : 0;
+            return DCRF_OK;
+        }
         static std::mutex mu_;
         static std::map<std::tuple<int, int, bool, int>, int> cache;
         int bucket = 0;

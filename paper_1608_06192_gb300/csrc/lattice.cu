@@ -11,7 +11,9 @@
 //   s0    = (2 pi)^{d/2} alpha^d / (d+1)^{d - 1/2}
 #include <cub/device/device_scan.cuh>
 
+#include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -558,11 +560,20 @@ static dcrf_status build_typed(dcrf_lattice lat, const float *feat, cudaStream_t
     // possible vertex count n_b (d+1)
     std::vector<int64_t> base(batch), mask(batch);
     int64_t slots = 0;
+    // testing hook: DCRF_TABLE_SLOTS caps every segment (power of two), so that
+    // the bounded probing and its DCRF_E_TABLE_FULL report can be exercised
+    int64_t cap_limit = 0;
+    if (const char *lim = std::getenv("DCRF_TABLE_SLOTS")) cap_limit = std::atoll(lim);
     for (int b = 0; b < batch; ++b) {
         int64_t nb = lat->point_off[b + 1] - lat->point_off[b];
         int64_t want = 2 * nb * D1 < 64 ? 64 : 2 * nb * D1;
         int64_t cap = 64;
         while (cap < want) cap <<= 1;
+        if (cap_limit >= 1) {
+            int64_t c2 = 1;
+            while (c2 * 2 <= cap_limit) c2 <<= 1;
+            cap = std::min(cap, c2);
+        }
         base[b] = slots;
         mask[b] = cap - 1;
         slots += cap;

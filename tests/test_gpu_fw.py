@@ -115,3 +115,14 @@ def test_fw_graph_path_matches_eager(dcrf):
     # conditional gradient can flip at a few pixels; all other rows agree
     d = np.abs(Y2.cpu().numpy() - Y1.cpu().numpy()).max(axis=1)
     assert np.mean(d > 1e-4) <= 0.01
+
+
+@pytest.mark.parametrize("variant", range(4))
+def test_fw_every_pixel_variant(dcrf, variant, monkeypatch):
+    # the autotuner chooses among these layouts of the pixel pass; each must
+    # follow the oracle's trajectory
+    monkeypatch.setenv("DCRF_PIXEL_VARIANT", str(variant))
+    p = S.make_problem(96, 64, 8, 21, seed=13)
+    for storage in ("f32", "f16"):
+        g, Y, rec = _run_fw(dcrf, [p], 15, storage=storage)
+        _check_against_oracle([p], g, Y, rec, 15, mono=1e-6 if storage == "f32" else 1e-4)

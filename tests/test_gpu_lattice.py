@@ -137,3 +137,17 @@ def test_invalid_arguments_rejected(dcrf):
     lat = dcrf.dcrf_lattice_build(torch.zeros((3, 2), dtype=torch.float32, device="cuda"))
     with pytest.raises(dcrf.DcrfError):
         dcrf.dcrf_filter(lat, torch.zeros((3, 65), device="cuda"))   # L > 64
+
+
+def test_table_full_is_reported(dcrf, monkeypatch):
+    # a table segment smaller than the vertex count: bounded probing gives up
+    # and the build returns DCRF_E_TABLE_FULL; the context stays usable
+    p = S.make_problem(40, 30, 5, 4, seed=14)
+    fb, fs = oracle_features(p)
+    f = torch.from_numpy(fs).cuda()
+    monkeypatch.setenv("DCRF_TABLE_SLOTS", "64")
+    with pytest.raises(dcrf.DcrfError) as e:
+        dcrf.dcrf_lattice_build(f)
+    assert e.value.status == -4
+    monkeypatch.delenv("DCRF_TABLE_SLOTS")
+    assert dcrf.dcrf_lattice_build(f).m > 64
