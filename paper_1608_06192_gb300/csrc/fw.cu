@@ -29,9 +29,14 @@ namespace {
 
 // Pixel-kernel variants (pixels per block = threads, minimum blocks per SM);
 // the autotuner picks one per (labels, storage, compatibility, size) at first use.
-constexpr int kPixVariants = 4;
-constexpr int kPixPB[kPixVariants] = {256, 256, 128, 128};
-constexpr int kPixMB[kPixVariants] = {4, 3, 8, 6};
+// Pixel-kernel modes: kFix gathers the corner rows of the common two-kernel
+// case (bilateral d = 5, spatial d = 2) with every index loaded up front;
+// kF2 accumulates the gathered rows with packed two-wide FP32 FMAs.
+constexpr int kFix = 1, kF2 = 2;
+constexpr int kPixVariants = 10;
+constexpr int kPixPB[kPixVariants] = {256, 256, 128, 128, 256, 256, 128, 256, 256, 256};
+constexpr int kPixMB[kPixVariants] = {4, 3, 8, 6, 4, 3, 6, 4, 3, 4};
+constexpr int kPixMode[kPixVariants] = {0, 0, 0, 0, kFix, kFix, kFix, kFix | kF2, kFix | kF2, kF2};
 constexpr int kVertBlock = 128;  // vertices per block
 constexpr int NS = 8;            // per-pixel scalar sums, see k_fw_pixel
 
@@ -120,6 +125,7 @@ struct PixArgs {
     float sumw;
     int L;
     int Ls;                // shared-memory row stride (odd)
+    bool y16;              // Y starts on a 16-byte boundary (lin always does)
     double *acc;           // [batch][NS]
     int *status;
 };
@@ -175,6 +181,10 @@ __device__ __forceinline__ void cp_async4(float *sdst, const float *gsrc) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gsrc) : "memory");
 }
+__device__ __forceinline__ void cp_async16(float *sdst, const float *gsrc) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
@@ -185,7 +195,14 @@ __device__ __forceinline__ void tile_load_async(const PixArgs &A, const Chunk &c
     const int L = A.L;
     const int64_t base = ch.begin * (int64_t)L;
     const int cnt = ch.count * L;
-    if (A.Ls == L) {
+    if (A.y16 && A.Ls == L && ((base | cnt) & 3) == 0) {
+        // dense rows, 16-byte aligned on both sides (Y, lin are 16-byte
+        // aligned allocations and sy, sl start on 16-byte shared offsets)
+        for (int i = 4 * threadIdx.x; i < cnt; i += 4 * blockDim.x) {
+            cp_async16(sy + i, A.Y + base + i);
+            cp_async16(sl + i, A.lin + base + i);
+        }
+    } else if (A.Ls == L) {
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
             cp_async4(sy + i, A.Y + base + i);
             cp_async4(sl + i, A.lin + base + i);
@@ -207,7 +224,10 @@ __device__ __forceinline__ void tile_store(const PixArgs &A, const Chunk &ch, co
     const int L = A.L;
     const int64_t base = ch.begin * (int64_t)L;
     const int cnt = ch.count * L;
-    if (A.Ls == L) {
+    if (A.y16 && A.Ls == L && ((base | cnt) & 3) == 0) {
+        for (int i = 4 * threadIdx.x; i < cnt; i += 4 * blockDim.x)
+            *reinterpret_cast<float4 *>(A.Y + base + i) = *reinterpret_cast<const float4 *>(sy + i);
+    } else if (A.Ls == L) {
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) A.Y[base + i] = sy[i];
     } else {
         int r = threadIdx.x / L, c = threadIdx.x - r * L;
@@ -221,8 +241,57 @@ __device__ __forceinline__ void tile_store(const PixArgs &A, const Chunk &ch, co
     }
 }
 
+// acc[8h .. 8h+7] += w o[0 .. 7], as scalar or packed FMAs (same rounding)
+template <int LP, bool F2>
+__device__ __forceinline__ void acc8(float (&acc)[LP], int h, float w, const float (&o)[8]) {
+    if constexpr (F2) {
+        const float2 w2 = make_float2(w, w);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float2 r = __ffma2_rn(w2, make_float2(o[2 * j], o[2 * j + 1]),
+                                        make_float2(acc[8 * h + 2 * j], acc[8 * h + 2 * j + 1]));
+            acc[8 * h + 2 * j] = r.x;
+            acc[8 * h + 2 * j + 1] = r.y;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[8 * h + j] += w * o[j];
+    }
+}
+
+// K~ y' for the two-kernel case with d+1 = DA and DB corners: every vertex id
+// and weight is loaded first, then every corner row, so that the dependent
+// loads of one pixel overlap (an absent corner reads row 0 with weight 0).
+template <int LP, typename TB, int DA, int DB, bool F2>
+__device__ __forceinline__ void gather_pair(const FwLat &la, const FwLat &lb, int64_t a, float (&ky)[LP]) {
+    int v[DA + DB];
+    float w[DA + DB];
+#pragma unroll
+    for (int k = 0; k < DA; ++k) {
+        v[k] = __ldg(la.pvid + a * DA + k);
+        w[k] = __ldg(la.pbary + a * DA + k) * la.ws0;
+    }
+#pragma unroll
+    for (int k = 0; k < DB; ++k) {
+        v[DA + k] = __ldg(lb.pvid + a * DB + k);
+        w[DA + k] = __ldg(lb.pbary + a * DB + k) * lb.ws0;
+    }
+    const TB *sa = slice_src<TB>(la), *sb = slice_src<TB>(lb);
+#pragma unroll
+    for (int k = 0; k < DA + DB; ++k) {
+        const int vk = v[k] < 0 ? 0 : v[k];
+        const float wk = v[k] < 0 ? 0.f : w[k];
+#pragma unroll
+        for (int h = 0; h < LP / 8; ++h) {
+            float o[8];
+            ld8(k < DA ? sa : sb, vk, LP, h, o);
+            acc8<LP, F2>(ky, h, wk, o);
+        }
+    }
+}
+
 // One chunk: every pixel of it (see the comment above PixArgs).
-template <int LP, typename TB, bool POTTS>
+template <int LP, typename TB, bool POTTS, int MODE>
 __device__ __forceinline__ void pixel_chunk(const PixArgs &A, const FwLats &F, const Chunk &ch, float *sy,
                                             const float *sl, float (&part)[NS]) {
     const int L = A.L;
@@ -242,9 +311,12 @@ __device__ __forceinline__ void pixel_chunk(const PixArgs &A, const FwLats &F, c
         float ky[LP];
 #pragma unroll
         for (int i = 0; i < LP; ++i) ky[i] = 0.f;
+        constexpr bool F2 = (MODE & kF2) != 0;
+        const bool fixed = (MODE & kFix) && F.nk == 2 && F.l[0].d1 == 6 && F.l[1].d1 == 3;
+        if (fixed) gather_pair<LP, TB, 6, 3, F2>(F.l[0], F.l[1], a, ky);
 #pragma unroll
         for (int mm = 0; mm < DCRF_MAX_KERNELS; ++mm) {
-            if (mm >= F.nk) break;
+            if (fixed || mm >= F.nk) break;
             const FwLat &lt = F.l[mm];
             const TB *src = slice_src<TB>(lt);
             for (int k = 0; k < lt.d1; ++k) {
@@ -255,16 +327,22 @@ __device__ __forceinline__ void pixel_chunk(const PixArgs &A, const FwLats &F, c
                 for (int h = 0; h < LP / 8; ++h) {
                     float o[8];
                     ld8(src, v, LP, h, o);
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) ky[8 * h + j] += w * o[j];
+                    acc8<LP, F2>(ky, h, w, o);
                 }
             }
         }
-        // y' = y + alpha (e_sold - y), read back from shared memory when needed
-        auto yp = [&](int i) {
-            const float v = yrow[i];
-            return start ? v : v + al * ((i == sold ? 1.f : 0.f) - v);
-        };
+        // y' = y + alpha (e_sold - y), written over the thread's shared-memory
+        // row once (it is stored back to Y after the block)
+        if (!start) {
+            float *yw = sy + t * A.Ls;
+#pragma unroll
+            for (int i = 0; i < LP; ++i)
+                if (i < L) {
+                    const float v = yw[i];
+                    yw[i] = v + al * ((i == sold ? 1.f : 0.f) - v);
+                }
+        }
+        auto yp = [&](int i) { return yrow[i]; };
         const float ca = A.c[a];
         float tot = 0.f, sy_ = 0.f;
 #pragma unroll
@@ -337,12 +415,6 @@ __device__ __forceinline__ void pixel_chunk(const PixArgs &A, const FwLats &F, c
             part[7] = sp;
         }
         A.s[a] = (uint8_t)sb;
-        if (!start) {
-            float *yw = sy + t * A.Ls;
-#pragma unroll
-            for (int i = 0; i < LP; ++i)
-                if (i < L) yw[i] = yp(i);
-        }
         // splat of the one-hot s' into Slat (FP32 reductions in L2)
 #pragma unroll
         for (int mm = 0; mm < DCRF_MAX_KERNELS; ++mm) {
@@ -358,9 +430,9 @@ __device__ __forceinline__ void pixel_chunk(const PixArgs &A, const FwLats &F, c
 
 // One block per chunk: the chunk's y and lin rows are copied to shared memory
 // (cp.async), every pixel is processed, y' is written back coalesced.
-template <int LP, typename TB, bool POTTS, int PB, int MB>
+template <int LP, typename TB, bool POTTS, int PB, int MB, int MODE>
 __global__ void __launch_bounds__(PB, MB) k_fw_pixel(PixArgs A, FwLats F) {
-    extern __shared__ float smem[];
+    extern __shared__ __align__(16) float smem[];
     float *sy = smem;
     float *sl = smem + PB * A.Ls;
     const Chunk ch = A.chunks[blockIdx.x];
@@ -369,7 +441,7 @@ __global__ void __launch_bounds__(PB, MB) k_fw_pixel(PixArgs A, FwLats F) {
     cp_wait<0>();
     __syncthreads();
     float part[NS];
-    pixel_chunk<LP, TB, POTTS>(A, F, ch, sy, sl, part);
+    pixel_chunk<LP, TB, POTTS, MODE>(A, F, ch, sy, sl, part);
     __syncthreads();
     if (A.alpha != nullptr) tile_store(A, ch, sy);
     block_reduce_f32<NS>(part, A.acc + (int64_t)ch.image * NS);
@@ -751,7 +823,7 @@ struct Solver {
         return DCRF_OK;
     }
 
-    template <int LPc, typename T, bool POT, int PB, int MB>
+    template <int LPc, typename T, bool POT, int PB, int MB, int MODE>
     dcrf_status pixel_v(float *Y, const float *phi, bool start, const double *alpha_override = nullptr) {
         PixArgs A;
         const int q = PB == 256 ? 0 : 1;
@@ -767,10 +839,11 @@ struct Solver {
         A.sumw = sumw;
         A.L = L;
         A.Ls = Ls;
+        A.y16 = (reinterpret_cast<uintptr_t>(Y) & 15) == 0;
         A.acc = acc;
         A.status = status;
         const size_t shm = 2 * (size_t)PB * Ls * sizeof(float);
-        auto kern = k_fw_pixel<LPc, T, POT, PB, MB>;
+        auto kern = k_fw_pixel<LPc, T, POT, PB, MB, MODE>;
         static bool attr = false;
         if (!attr) {
             DCRF_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
@@ -789,15 +862,24 @@ struct Solver {
     template <int LPc, typename T, bool POT>
     dcrf_status pixel_var(int v, float *Y, const float *phi, bool start, const double *al = nullptr) {
         if constexpr (LPc == 24 && POT) {
+#define DCRF_PIX_CASE(V) \
+    case V: return pixel_v<LPc, T, POT, kPixPB[V], kPixMB[V], kPixMode[V]>(Y, phi, start, al)
             switch (v) {
-            case 0: return pixel_v<LPc, T, POT, kPixPB[0], kPixMB[0]>(Y, phi, start, al);
-            case 1: return pixel_v<LPc, T, POT, kPixPB[1], kPixMB[1]>(Y, phi, start, al);
-            case 2: return pixel_v<LPc, T, POT, kPixPB[2], kPixMB[2]>(Y, phi, start, al);
-            default: return pixel_v<LPc, T, POT, kPixPB[3], kPixMB[3]>(Y, phi, start, al);
+                DCRF_PIX_CASE(1);
+                DCRF_PIX_CASE(2);
+                DCRF_PIX_CASE(3);
+                DCRF_PIX_CASE(4);
+                DCRF_PIX_CASE(5);
+                DCRF_PIX_CASE(6);
+                DCRF_PIX_CASE(7);
+                DCRF_PIX_CASE(8);
+                DCRF_PIX_CASE(9);
+            default: return pixel_v<LPc, T, POT, kPixPB[0], kPixMB[0], kPixMode[0]>(Y, phi, start, al);
             }
+#undef DCRF_PIX_CASE
         } else {
             (void)v;
-            return pixel_v<LPc, T, POT, kPixPB[0], (LPc <= 24 ? kPixMB[0] : 2)>(Y, phi, start, al);
+            return pixel_v<LPc, T, POT, kPixPB[0], (LPc <= 24 ? kPixMB[0] : 2), 0>(Y, phi, start, al);
         }
     }
 

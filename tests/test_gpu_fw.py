@@ -1,4 +1,6 @@
 """GPU parity of Frank-Wolfe (Algorithm 1, Appendix B) and CCCP (Algorithm 2)."""
+import hashlib
+
 import numpy as np
 import pytest
 
@@ -19,10 +21,25 @@ def _run_fw(dcrf, probs, iters, storage="f32", mu=None):
     return g, Y.cpu().numpy(), rec
 
 
+_ORACLE_RUNS = {}
+
+
+def _oracle_fw(p, mu, iters):
+    h = hashlib.sha1()
+    for arr in (p.rgb, p.unaries, p.y0, np.asarray(p.weights), np.asarray(p.thetas)):
+        h.update(np.ascontiguousarray(arr).tobytes())
+    key = (h.hexdigest(), None if mu is None else np.asarray(mu).tobytes(), iters)
+    if key not in _ORACLE_RUNS:
+        c = oracle_crf(p, mu)
+        _ORACLE_RUNS.clear()
+        _ORACLE_RUNS[key] = (c,) + tuple(qp.frank_wolfe(c, p.y0, iters))
+    c, y_o, _, rec_o = _ORACLE_RUNS[key]
+    return c, y_o, rec_o
+
+
 def _check_against_oracle(probs, g, Y, rec, iters, mu=None, tol=ENERGY_TOL, mono=1e-6):
     for b, p in enumerate(probs):
-        c = oracle_crf(p, mu)
-        y_o, _, rec_o = qp.frank_wolfe(c, p.y0, iters)
+        c, y_o, rec_o = _oracle_fw(p, mu, iters)
         e_o = rec_o[:, 0]
         scale = np.abs(e_o).max()
         # per-iteration energy and the final relaxed energy
@@ -117,10 +134,10 @@ def test_fw_graph_path_matches_eager(dcrf):
     assert np.mean(d > 1e-4) <= 0.01
 
 
-@pytest.mark.parametrize("variant", range(4))
+@pytest.mark.parametrize("variant", range(10))
 def test_fw_every_pixel_variant(dcrf, variant, monkeypatch):
-    # the autotuner chooses among these layouts of the pixel pass; each must
-    # follow the oracle's trajectory
+    # the autotuner chooses among these layouts of the pixel pass (block
+    # shapes, index prefetch, packed FMAs); each must follow the oracle
     monkeypatch.setenv("DCRF_PIXEL_VARIANT", str(variant))
     p = S.make_problem(96, 64, 8, 21, seed=13)
     for storage in ("f32", "f16"):
