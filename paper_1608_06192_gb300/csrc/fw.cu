@@ -31,12 +31,14 @@ namespace {
 // the autotuner picks one per (labels, storage, compatibility, size) at first use.
 // Pixel-kernel modes: kFix gathers the corner rows of the common two-kernel
 // case (bilateral d = 5, spatial d = 2) with every index loaded up front;
-// kF2 accumulates the gathered rows with packed two-wide FP32 FMAs.
+// kF2 accumulates the gathered rows with packed two-wide FP32 FMAs.  (A
+// shared-memory hash aggregation of the splat was measured 2x slower than
+// plain FP32 reductions in L2: many pixels of a block hit the same key.)
 constexpr int kFix = 1, kF2 = 2;
-constexpr int kPixVariants = 10;
-constexpr int kPixPB[kPixVariants] = {256, 256, 128, 128, 256, 256, 128, 256, 256, 256};
-constexpr int kPixMB[kPixVariants] = {4, 3, 8, 6, 4, 3, 6, 4, 3, 4};
-constexpr int kPixMode[kPixVariants] = {0, 0, 0, 0, kFix, kFix, kFix, kFix | kF2, kFix | kF2, kF2};
+constexpr int kPixVariants = 7;
+constexpr int kPixPB[kPixVariants] = {256, 128, 256, 256, 128, 256, 256};
+constexpr int kPixMB[kPixVariants] = {4, 8, 4, 3, 6, 3, 4};
+constexpr int kPixMode[kPixVariants] = {0, 0, kFix, kFix, kFix, kFix | kF2, kFix | kF2};
 constexpr int kVertBlock = 128;  // vertices per block
 constexpr int NS = 8;            // per-pixel scalar sums, see k_fw_pixel
 
@@ -126,7 +128,7 @@ struct PixArgs {
     int L;
     int Ls;                // shared-memory row stride (odd)
     bool y16;              // Y starts on a 16-byte boundary (lin always does)
-    double *acc;           // [batch][NS]
+    float *cpart;          // [chunks][NS][2] per-chunk sums (hi, lo)
     int *status;
 };
 
@@ -152,27 +154,53 @@ __device__ __forceinline__ void ld8(const __half *p, int64_t row, int LP, int h,
     o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y; o[4] = c.x; o[5] = c.y; o[6] = d.x; o[7] = d.y;
 }
 
-// Sum over the block: FP32 within each warp, FP64 across warps and blocks.
+// s + e = a + b exactly (Knuth's two-sum; no FMA contraction applies).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+}
+
+// (hi, lo) += (h2, l2) with the rounding error of hi + h2 kept in lo.
+__device__ __forceinline__ void add_comp(float &hi, float &lo, float h2, float l2) {
+    float s, e;
+    two_sum(hi, h2, s, e);
+    hi = s;
+    lo += l2 + e;
+}
+
+// Sum over the block: FP32 within each warp, then across warps as a
+// compensated (hi, lo) pair; the block's N pairs are stored to
+// out[0 .. 2N) (one row of per-chunk partials, summed across chunks by the
+// step kernel).  No FP64 arithmetic here: the FP64 pipe of this part is
+// narrow, and the pairs keep the sums as accurate as FP64 across warps.
 template <int N>
-__device__ __forceinline__ void block_reduce_f32(float (&v)[N], double *acc) {
-    __shared__ double red[32][N];
+__device__ __forceinline__ void block_sum_f32(float (&v)[N], float *out) {
+    __shared__ float red[32][N];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < N; ++q) {
         float x = v[q];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0) red[warp][q] = (double)x;
+        if (lane == 0) red[warp][q] = x;
     }
     __syncthreads();
     if (warp == 0) {
         const int nw = blockDim.x >> 5;
 #pragma unroll
         for (int q = 0; q < N; ++q) {
-            double x = lane < nw ? red[lane][q] : 0.0;
+            float hi = lane < nw ? red[lane][q] : 0.f, lo = 0.f;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-            if (lane == 0) atomicAdd(acc + q, x);
+            for (int o = 16; o > 0; o >>= 1) {
+                const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
+                const float l2 = __shfl_down_sync(0xffffffffu, lo, o);
+                add_comp(hi, lo, h2, l2);
+            }
+            if (lane == 0) {
+                out[2 * q] = hi;
+                out[2 * q + 1] = lo;
+            }
         }
     }
 }
@@ -415,7 +443,9 @@ __device__ __forceinline__ void pixel_chunk(const PixArgs &A, const FwLats &F, c
             part[7] = sp;
         }
         A.s[a] = (uint8_t)sb;
-        // splat of the one-hot s' into Slat (FP32 reductions in L2)
+        // splat of the one-hot s' into Slat (FP32 reductions in L2).  A delta
+        // update (+b at s', -b at s) does not pay: along the Frank-Wolfe path
+        // almost every pixel's argmin moves at every iteration.
 #pragma unroll
         for (int mm = 0; mm < DCRF_MAX_KERNELS; ++mm) {
             if (mm >= F.nk) break;
@@ -444,7 +474,7 @@ __global__ void __launch_bounds__(PB, MB) k_fw_pixel(PixArgs A, FwLats F) {
     pixel_chunk<LP, TB, POTTS, MODE>(A, F, ch, sy, sl, part);
     __syncthreads();
     if (A.alpha != nullptr) tile_store(A, ch, sy);
-    block_reduce_f32<NS>(part, A.acc + (int64_t)ch.image * NS);
+    block_sum_f32<NS>(part, A.cpart + (int64_t)blockIdx.x * 2 * NS);
 }
 
 // Blur pass `p` of every lattice in one launch (lattice m takes part while
@@ -515,6 +545,37 @@ __global__ void __launch_bounds__(256) k_fw_blur(BlurSet B, int p) {
     const int D = lt.d1 - 1;
     T *out = ((D - p) % 2 == 0) ? (T *)lt.dst : (T *)lt.tmp;
     const int2 nb = reinterpret_cast<const int2 *>(lt.nbr)[v * lt.d1 + p];
+    if constexpr (sizeof(T) == 2 && LP <= 24) {
+        if (p > 0) {
+            // half rows: every 16-byte load of the three rows is issued before
+            // any arithmetic or store (the output is never an input, but the
+            // compiler cannot know that); raw halves keep the registers low
+            const uint4 *in = reinterpret_cast<const uint4 *>(((D - p + 1) % 2 == 0) ? lt.dst : lt.tmp);
+            uint4 c[LP / 8], a[LP / 8], b[LP / 8];
+            const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+            for (int q = 0; q < LP / 8; ++q) {
+                c[q] = in[v * (LP / 8) + q];
+                a[q] = nb.x >= 0 ? in[(int64_t)nb.x * (LP / 8) + q] : z;
+                b[q] = nb.y >= 0 ? in[(int64_t)nb.y * (LP / 8) + q] : z;
+            }
+#pragma unroll
+            for (int q = 0; q < LP / 8; ++q) {
+                const __half2 *hc = reinterpret_cast<const __half2 *>(&c[q]);
+                const __half2 *ha = reinterpret_cast<const __half2 *>(&a[q]);
+                const __half2 *hb = reinterpret_cast<const __half2 *>(&b[q]);
+                float o[8];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float2 fc = __half22float2(hc[j]), fa = __half22float2(ha[j]), fb = __half22float2(hb[j]);
+                    o[2 * j] = 0.5f * fc.x + 0.25f * fa.x + 0.25f * fb.x;
+                    o[2 * j + 1] = 0.5f * fc.y + 0.25f * fa.y + 0.25f * fb.y;
+                }
+                row_store(out, v, LP, q, o);
+            }
+            return;
+        }
+    }
 #pragma unroll
     for (int q = 0; q < LP / 8; ++q) {
         float c[8], a[8], b[8];
@@ -537,20 +598,21 @@ __global__ void __launch_bounds__(256) k_fw_blur(BlurSet B, int p) {
 }
 
 // Lattice dot products for the line search:
-//   lacc[0] += w s0 sum_v sum_ij mu_ij Ylat[v][i] BS[v][j]   (= <y, K~-part of Psi s>)
-//   lacc[1] += w s0 sum_v sum_ij mu_ij Slat[v][i] BS[v][j]   (= <s, K~-part of Psi s>)
+//   0: w s0 sum_v sum_ij mu_ij Ylat[v][i] BS[v][j]   (= <y, K~-part of Psi s>)
+//   1: w s0 sum_v sum_ij mu_ij Slat[v][i] BS[v][j]   (= <s, K~-part of Psi s>)
+// summed per vertex chunk in FP32.
 struct DotArgs {
     const Chunk *chunks;    // vertex chunks of lattice `which`
     const float *mu;
     int L;
     int which;
-    double *lacc;           // [batch][2]
+    float *vpart;           // [vertex chunks of this lattice][2][2] per-chunk sums (hi, lo)
 };
 
 template <int LP, typename T, bool POTTS>
 __global__ void __launch_bounds__(kVertBlock) k_fw_latdot(DotArgs A, FwLat lt) {
     const Chunk ch = A.chunks[blockIdx.x];
-    double part[2] = {0.0, 0.0};
+    float part[2] = {0.f, 0.f};
     if ((int)threadIdx.x < ch.count) {
         const int64_t v = ch.begin + threadIdx.x;
         float yv[LP], sv[LP], bv[LP];
@@ -583,20 +645,84 @@ __global__ void __launch_bounds__(kVertBlock) k_fw_latdot(DotArgs A, FwLat lt) {
                 ps += sv[i] * mb;
             }
         }
-        part[0] = (double)lt.ws0 * py;
-        part[1] = (double)lt.ws0 * ps;
+        part[0] = lt.ws0 * py;
+        part[1] = lt.ws0 * ps;
     }
-    block_reduce_add<2>(part, A.lacc + (int64_t)ch.image * 2);
+    block_sum_f32<2>(part, A.vpart + (int64_t)blockIdx.x * 4);
 }
 
-// Step size and record of one iteration, one thread per image.
-__global__ void k_fw_alpha(int batch, double *acc, double *lacc, double *alpha, dcrf_fw_record *rec,
-                           int *counter, int *status) {
+// Per-image FP64 sums of per-chunk FP32 partials: chunks [range[b], range[b+1])
+// of rows of width W, summed into out[0 .. W) by the calling block.
+struct PartSums {
+    const float *cpart;                    // [pixel chunks][NS][2]
+    const int *crange;                     // [batch + 1]
+    const float *vpart;                    // [vertex chunks of all lattices][2][2]
+    const int *vrange;                     // [nk][batch + 1] into vpart rows
+    int nk;
+    int batch;
+};
+
+// Per-image sums of rows of W compensated (hi, lo) pairs, compensated FP32
+// throughout (each thread's strided rows, warps, then across warps); each sum
+// becomes FP64 once, as hi + lo.  The result is valid in thread 0.
+template <int W>
+__device__ __forceinline__ void image_sums(const float *part, int c0, int c1, double (&out)[W]) {
+    __shared__ float rh[32][W], rl[32][W];
+    __shared__ double col[W];
+    float hi[W], lo[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) hi[q] = lo[q] = 0.f;
+    for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x)
+#pragma unroll
+        for (int q = 0; q < W; ++q) add_comp(hi[q], lo[q], part[((int64_t)c * W + q) * 2], part[((int64_t)c * W + q) * 2 + 1]);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_down_sync(0xffffffffu, hi[q], o);
+            const float l2 = __shfl_down_sync(0xffffffffu, lo[q], o);
+            add_comp(hi[q], lo[q], h2, l2);
+        }
+        if (lane == 0) {
+            rh[warp][q] = hi[q];
+            rl[warp][q] = lo[q];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < W) {
+        float h = 0.f, l = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) add_comp(h, l, rh[w][threadIdx.x], rl[w][threadIdx.x]);
+        col[threadIdx.x] = (double)h + (double)l;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int q = 0; q < W; ++q) out[q] = col[q];
+    __syncthreads();
+}
+
+__device__ __forceinline__ void pixel_sums(const PartSums &P, int b, double (&sg)[NS]) {
+    image_sums<NS>(P.cpart, P.crange[b], P.crange[b + 1], sg);
+}
+
+// Step size and record of one iteration, one block per image; the last block
+// to finish advances the iteration counter.
+__global__ void k_fw_alpha(PartSums P, double *alpha, dcrf_fw_record *rec, int *counter, int *ticket,
+                           int *status) {
+    const int b = blockIdx.x;
     const int t = *counter;
-    for (int b = threadIdx.x; b < batch; b += blockDim.x) {
-        const double *sg = acc + (int64_t)b * NS;
-        const double yPs = lacc[2 * b + 0] + sg[4];
-        const double sPs = lacc[2 * b + 1] + sg[5];
+    double sg[NS];
+    pixel_sums(P, b, sg);
+    double yPs = sg[4], sPs = sg[5];
+    for (int m = 0; m < P.nk; ++m) {
+        double lt[2];
+        const int *vr = P.vrange + m * (P.batch + 1);
+        image_sums<2>(P.vpart, vr[b], vr[b + 1], lt);
+        yPs += lt[0];
+        sPs += lt[1];
+    }
+    if (threadIdx.x == 0) {
         const double A = sPs - sg[3] - yPs + sg[1];
         const double B = sg[2] - sg[0] + yPs - 2.0 * sg[1] + sg[3];
         double al;
@@ -616,14 +742,14 @@ __global__ void k_fw_alpha(int batch, double *acc, double *lacc, double *alpha, 
             r.alpha = al;
             r.A = A;
             r.B = B;
-            rec[(int64_t)t * batch + b] = r;
+            rec[(int64_t)t * P.batch + b] = r;
         }
-        for (int q = 0; q < NS; ++q) acc[(int64_t)b * NS + q] = 0.0;
-        lacc[2 * b] = 0.0;
-        lacc[2 * b + 1] = 0.0;
+        __threadfence();
+        if (atomicAdd(ticket, 1) == (int)gridDim.x - 1) {
+            *ticket = 0;
+            *counter = t + 1;
+        }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) *counter = t + 1;
 }
 
 // Ylat += alpha (Slat - Ylat); BY += alpha (BS - BY) (and its half copy); Slat = 0.
@@ -670,11 +796,10 @@ __global__ void k_fw_lin(int64_t n, int L, const float *phi, const float *c, con
     lin[i] = p - scale * musum[l] * c[a] * yv;
 }
 
-__global__ void k_fw_qp_energy(int batch, const double *acc, double *out) {
-    for (int b = threadIdx.x; b < batch; b += blockDim.x) {
-        const double *sg = acc + (int64_t)b * NS;
-        out[b] = sg[7] + sg[1] - sg[6];   // phi^T y + y^T (Psi + D) y - y^T D y
-    }
+__global__ void k_fw_qp_energy(PartSums P, double *out) {
+    double sg[NS];
+    pixel_sums(P, blockIdx.x, sg);
+    if (threadIdx.x == 0) out[blockIdx.x] = sg[7] + sg[1] - sg[6];   // phi^T y + y^T (Psi + D) y - y^T D y
 }
 
 inline unsigned nblocks(int64_t work, int threads) { return (unsigned)((work + threads - 1) / threads); }
@@ -697,8 +822,12 @@ struct Solver {
     std::vector<int> n_vchunks;
     float *mu = nullptr, *musum = nullptr, *c = nullptr, *lin = nullptr;
     uint8_t *sidx = nullptr;
-    double *acc = nullptr, *lacc = nullptr, *alpha = nullptr;
-    int *counter = nullptr;
+    float *cpart = nullptr, *vpart = nullptr;  // per-chunk FP32 partial sums
+    int *crange = nullptr;                     // [2][batch + 1] pixel-chunk range per image
+    int *vrange = nullptr;                     // [nk][batch + 1] vertex-chunk rows per image
+    std::vector<int64_t> voff;                 // first vpart row of each lattice
+    double *alpha = nullptr;
+    int *counter = nullptr, *ticket = nullptr;
     dcrf_fw_record *rec = nullptr;
     int *status = nullptr;
 
@@ -744,6 +873,7 @@ struct Solver {
         DCRF_TRY(cudaMemcpyAsync(musum, ms_h.data(), L * sizeof(float), cudaMemcpyHostToDevice, s));
         // lattice workspaces
         F.nk = nk;
+        std::vector<int> vrange_h;
         for (int m = 0; m < nk; ++m) {
             FwLat &l = F.l[m];
             const dcrf_lattice lat = lattices[m];
@@ -773,25 +903,40 @@ struct Solver {
                 DCRF_TRY(cudaMemcpyAsync(chd, ch.data(), ch.size() * sizeof(Chunk), cudaMemcpyHostToDevice, s));
             vchunks.push_back(chd);
             n_vchunks.push_back((int)ch.size());
+            voff.push_back(m == 0 ? 0 : voff[m - 1] + n_vchunks[m - 1]);
+            for (int b = 0; b <= batch; ++b) vrange_h.push_back((int)voff[m]);
+            for (const Chunk &c : ch) vrange_h[(size_t)m * (batch + 1) + c.image + 1]++;
+            for (int b = 0; b < batch; ++b)
+                vrange_h[(size_t)m * (batch + 1) + b + 1] += vrange_h[(size_t)m * (batch + 1) + b] - (int)voff[m];
         }
+        std::vector<int> crange_h(2 * (batch + 1), 0);
         for (int q = 0; q < 2; ++q) {
             auto pc = make_chunks(lattices[0]->point_off, q == 0 ? 256 : 128);
             n_chunks_pb[q] = (int)pc.size();
             DCRF_CHECK_STATUS(sc.get(&chunks_pb[q], pc.size() > 0 ? pc.size() : 1));
             if (!pc.empty())
                 DCRF_TRY(cudaMemcpyAsync(chunks_pb[q], pc.data(), pc.size() * sizeof(Chunk), cudaMemcpyHostToDevice, s));
+            for (const Chunk &c : pc) crange_h[q * (batch + 1) + c.image + 1]++;
+            for (int b = 0; b < batch; ++b) crange_h[q * (batch + 1) + b + 1] += crange_h[q * (batch + 1) + b];
         }
+        const int64_t nv = nk > 0 ? voff[nk - 1] + n_vchunks[nk - 1] : 0;
+        DCRF_CHECK_STATUS(sc.get(&cpart, (size_t)std::max(1, std::max(n_chunks_pb[0], n_chunks_pb[1])) * NS * 2));
+        DCRF_CHECK_STATUS(sc.get(&vpart, (size_t)std::max<int64_t>(1, nv) * 4));
+        DCRF_CHECK_STATUS(sc.get(&crange, crange_h.size()));
+        DCRF_CHECK_STATUS(sc.get(&vrange, std::max<size_t>(1, vrange_h.size())));
+        DCRF_TRY(cudaMemcpyAsync(crange, crange_h.data(), crange_h.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+        if (!vrange_h.empty())
+            DCRF_TRY(cudaMemcpyAsync(vrange, vrange_h.data(), vrange_h.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                     s));
+
         DCRF_CHECK_STATUS(sc.get(&c, (size_t)(n > 0 ? n : 1)));
         DCRF_CHECK_STATUS(sc.get(&lin, (size_t)(n > 0 ? n : 1) * L));
         DCRF_CHECK_STATUS(sc.get(&sidx, (size_t)(n > 0 ? n : 1)));
-        DCRF_CHECK_STATUS(sc.get(&acc, (size_t)batch * NS));
-        DCRF_CHECK_STATUS(sc.get(&lacc, (size_t)batch * 2));
         DCRF_CHECK_STATUS(sc.get(&alpha, (size_t)batch));
-        DCRF_CHECK_STATUS(sc.get(&counter, 1));
+        DCRF_CHECK_STATUS(sc.get(&counter, 2));
+        ticket = counter + 1;
         DCRF_CHECK_STATUS(sc.get(&rec, (size_t)batch * (max_records > 0 ? max_records : 1)));
-        DCRF_TRY(cudaMemsetAsync(acc, 0, batch * NS * sizeof(double), s));
-        DCRF_TRY(cudaMemsetAsync(lacc, 0, batch * 2 * sizeof(double), s));
-        DCRF_TRY(cudaMemsetAsync(counter, 0, sizeof(int), s));
+        DCRF_TRY(cudaMemsetAsync(counter, 0, 2 * sizeof(int), s));
         // c_a and lin = phi - d
         const float *ones_h[DCRF_MAX_KERNELS];
         for (int m = 0; m < nk; ++m) ones_h[m] = lattices[m]->ones;
@@ -823,6 +968,19 @@ struct Solver {
         return DCRF_OK;
     }
 
+    // Partial-sum layout of the chosen pixel variant (after the first pixel pass).
+    PartSums parts() const {
+        PartSums P;
+        const int q = kPixPB[variant < 0 ? 0 : variant] == 256 ? 0 : 1;
+        P.cpart = cpart;
+        P.crange = crange + q * (batch + 1);
+        P.vpart = vpart;
+        P.vrange = vrange;
+        P.nk = nk;
+        P.batch = batch;
+        return P;
+    }
+
     template <int LPc, typename T, bool POT, int PB, int MB, int MODE>
     dcrf_status pixel_v(float *Y, const float *phi, bool start, const double *alpha_override = nullptr) {
         PixArgs A;
@@ -840,7 +998,7 @@ struct Solver {
         A.L = L;
         A.Ls = Ls;
         A.y16 = (reinterpret_cast<uintptr_t>(Y) & 15) == 0;
-        A.acc = acc;
+        A.cpart = cpart;
         A.status = status;
         const size_t shm = 2 * (size_t)PB * Ls * sizeof(float);
         auto kern = k_fw_pixel<LPc, T, POT, PB, MB, MODE>;
@@ -871,9 +1029,6 @@ struct Solver {
                 DCRF_PIX_CASE(4);
                 DCRF_PIX_CASE(5);
                 DCRF_PIX_CASE(6);
-                DCRF_PIX_CASE(7);
-                DCRF_PIX_CASE(8);
-                DCRF_PIX_CASE(9);
             default: return pixel_v<LPc, T, POT, kPixPB[0], kPixMB[0], kPixMode[0]>(Y, phi, start, al);
             }
 #undef DCRF_PIX_CASE
@@ -933,7 +1088,6 @@ struct Solver {
         cudaEventDestroy(e1);
         for (int m = 0; m < nk; ++m)
             DCRF_TRY(cudaMemsetAsync(F.l[m].Slat, 0, (size_t)(F.l[m].m > 0 ? F.l[m].m : 1) * Lp * sizeof(float), s));
-        DCRF_TRY(cudaMemsetAsync(acc, 0, batch * NS * sizeof(double), s));
         variant = arg;
         std::lock_guard<std::mutex> lk(mu_);
         cache[key] = arg;
@@ -1011,7 +1165,7 @@ struct Solver {
         A.mu = mu;
         A.L = L;
         A.which = which;
-        A.lacc = lacc;
+        A.vpart = vpart + 4 * voff[which];
         if (n_vchunks[which] > 0) {
             ProfScope ps(P_FW_LATDOT, s);
             k_fw_latdot<LPc, T, POT><<<n_vchunks[which], kVertBlock, 0, s>>>(A, F.l[which]);
@@ -1039,7 +1193,7 @@ struct Solver {
         for (int m = 0; m < nk; ++m) DCRF_CHECK_STATUS(latdot(m));
         {
             ProfScope ps(P_FW_ALPHA, s);
-            k_fw_alpha<<<1, 256, 0, s>>>(batch, acc, lacc, alpha, rec, counter, status);
+            k_fw_alpha<<<batch, 256, 0, s>>>(parts(), alpha, rec, counter, ticket, status);
         }
         DCRF_LAUNCHED();
         const int G = Lp / 4;
@@ -1122,7 +1276,7 @@ extern "C" dcrf_status dcrf_dc_cccp(const float *unaries, const dcrf_lattice *la
     DCRF_CHECK_STATUS(S.sc.get(&qe, (size_t)(outer + 1) * S.batch));
     // S_QP at y^0
     DCRF_CHECK_STATUS(S.pixel(Y, unaries, true));
-    k_fw_qp_energy<<<1, 256, 0, s>>>(S.batch, S.acc, qe);
+    k_fw_qp_energy<<<S.batch, 256, 0, s>>>(S.parts(), qe);
     DCRF_LAUNCHED();
     const int G = S.Lp / 4;
     (void)G;
@@ -1133,10 +1287,9 @@ extern "C" dcrf_status dcrf_dc_cccp(const float *unaries, const dcrf_lattice *la
         for (int m = 0; m < S.nk; ++m)
             DCRF_TRY(cudaMemsetAsync(S.F.l[m].Slat, 0,
                                      (size_t)(S.F.l[m].m > 0 ? S.F.l[m].m : 1) * S.Lp * sizeof(float), s));
-        DCRF_TRY(cudaMemsetAsync(S.acc, 0, S.batch * NS * sizeof(double), s));
         DCRF_CHECK_STATUS(S.pixel(Y, inner == 0 ? unaries : nullptr, true));
         DCRF_CHECK_STATUS(S.run(Y, inner, unaries));
-        k_fw_qp_energy<<<1, 256, 0, s>>>(S.batch, S.acc, qe + (int64_t)(o + 1) * S.batch);
+        k_fw_qp_energy<<<S.batch, 256, 0, s>>>(S.parts(), qe + (int64_t)(o + 1) * S.batch);
         DCRF_LAUNCHED();
     }
     if (qp_energy) {

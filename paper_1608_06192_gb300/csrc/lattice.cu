@@ -9,6 +9,7 @@
 //   m_i   = rint(x_i / (d+1)), rank correction, barycentric weights
 //   blur  = d+1 Jacobi passes [1/4, 1/2, 1/4] along w_j = (d+1) e_j - 1
 //   s0    = (2 pi)^{d/2} alpha^d / (d+1)^{d - 1/2}
+#include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
 
 #include <algorithm>
@@ -265,6 +266,39 @@ __global__ void k_embed_insert(const float *__restrict__ feat, int64_t n, EmbedP
         }
         pslot[a * D1 + k] = found;
     }
+}
+
+// Vertex numbering by first touch: first[slot] = the lowest incidence index
+// a (d+1) + k that lands on the slot.  Vertices are then numbered in that
+// order, so pixels that are close in raster order find their corners close
+// in memory (and the numbering no longer depends on the hash layout).
+__global__ void k_first_touch(const int64_t *__restrict__ pslot, int64_t count,
+                              unsigned long long *__restrict__ first) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const int64_t slot = pslot[i];
+    if (slot >= 0 && first[slot] > (unsigned long long)i) atomicMin(first + slot, (unsigned long long)i);
+}
+
+__global__ void k_vertex_first(const unsigned long long *__restrict__ first, int64_t slots,
+                               const int32_t *__restrict__ flag, const int32_t *__restrict__ scan,
+                               unsigned long long *__restrict__ vkey, int32_t *__restrict__ vold) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= slots || !flag[i]) return;
+    const int v = scan[i];
+    vkey[v] = first[i];
+    vold[v] = v;
+}
+
+__global__ void k_rank_of(const int32_t *__restrict__ vold_sorted, int64_t m, int32_t *__restrict__ rank) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r < m) rank[vold_sorted[r]] = (int32_t)r;
+}
+
+__global__ void k_slot_ids(const int32_t *__restrict__ flag, const int32_t *__restrict__ scan,
+                           const int32_t *__restrict__ rank, int64_t slots, int32_t *__restrict__ ids) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < slots) ids[i] = flag[i] ? rank[scan[i]] : 0;
 }
 
 __global__ void k_occupied(const unsigned long long *__restrict__ table, int64_t slots,
@@ -626,18 +660,50 @@ static dcrf_status build_typed(dcrf_lattice lat, const float *feat, cudaStream_t
     lat->m = lat->vert_off[batch];
     const int64_t m = lat->m;
 
+    // renumber the vertices by first touch (image ranges are unchanged: every
+    // vertex of image b is first touched by a point of image b)
+    int32_t *ids = scan;
+    if (m > 1) {
+        unsigned long long *first, *vkey, *vkey2;
+        int32_t *vold, *vold2, *rank;
+        DCRF_CHECK_STATUS(sc.get(&first, slots));
+        DCRF_CHECK_STATUS(sc.get(&vkey, m));
+        DCRF_CHECK_STATUS(sc.get(&vkey2, m));
+        DCRF_CHECK_STATUS(sc.get(&vold, m));
+        DCRF_CHECK_STATUS(sc.get(&vold2, m));
+        DCRF_CHECK_STATUS(sc.get(&rank, m));
+        DCRF_CHECK_STATUS(sc.get(&ids, slots));
+        DCRF_TRY(cudaMemsetAsync(first, 0xFF, slots * sizeof(unsigned long long), s));
+        k_first_touch<<<blocks_for(n * D1, 256), 256, 0, s>>>(pslot, n * D1, first);
+        DCRF_LAUNCHED();
+        k_vertex_first<<<blocks_for(slots, 256), 256, 0, s>>>(first, slots, flag, scan, vkey, vold);
+        DCRF_LAUNCHED();
+        int end_bit = 1;
+        while (end_bit < 64 && ((unsigned long long)(n * D1) >> end_bit) != 0) ++end_bit;
+        size_t sort_bytes = 0;
+        DCRF_TRY(cub::DeviceRadixSort::SortPairs(nullptr, sort_bytes, vkey, vkey2, vold, vold2, (int)m, 0, end_bit, s));
+        char *sort_tmp;
+        DCRF_CHECK_STATUS(sc.get(&sort_tmp, sort_bytes));
+        DCRF_TRY(cub::DeviceRadixSort::SortPairs(sort_tmp, sort_bytes, vkey, vkey2, vold, vold2, (int)m, 0, end_bit,
+                                                 s));
+        k_rank_of<<<blocks_for(m, 256), 256, 0, s>>>(vold2, m, rank);
+        DCRF_LAUNCHED();
+        k_slot_ids<<<blocks_for(slots, 256), 256, 0, s>>>(flag, scan, rank, slots, ids);
+        DCRF_LAUNCHED();
+    }
+
     DCRF_TRY(cudaMalloc(&lat->keys, (m > 0 ? m : 1) * D * sizeof(int32_t)));
     DCRF_TRY(cudaMalloc(&lat->vimg, (m > 0 ? m : 1) * sizeof(int32_t)));
     DCRF_TRY(cudaMalloc(&lat->nbr, (m > 0 ? m : 1) * D1 * 2 * sizeof(int32_t)));
-    k_finalize_slots<D><<<blocks_for(slots, 256), 256, 0, s>>>(table, slots, scan, base_d, batch, lat->keys,
+    k_finalize_slots<D><<<blocks_for(slots, 256), 256, 0, s>>>(table, slots, ids, base_d, batch, lat->keys,
                                                                lat->vimg);
     DCRF_LAUNCHED();
     if (n > 0) {
-        k_assign_vid<<<blocks_for(n * D1, 256), 256, 0, s>>>(pslot, n * D1, scan, lat->pvid);
+        k_assign_vid<<<blocks_for(n * D1, 256), 256, 0, s>>>(pslot, n * D1, ids, lat->pvid);
         DCRF_LAUNCHED();
     }
     if (m > 0) {
-        k_neighbours<D><<<blocks_for(m, 128), 128, 0, s>>>(lat->keys, lat->vimg, m, table, scan, base_d, mask_d,
+        k_neighbours<D><<<blocks_for(m, 128), 128, 0, s>>>(lat->keys, lat->vimg, m, table, ids, base_d, mask_d,
                                                            lat->nbr);
         DCRF_LAUNCHED();
     }
