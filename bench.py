@@ -178,6 +178,23 @@ class ClockSampler:
         return out
 
 
+def measured_traffic(kind, n):
+    """DRAM bytes per launch of the pixel kernel from the committed ncu capture
+    (profiles/fw_pixel_traffic.json), scaled by pixels; None when the kernel
+    source changed since the capture or for other kernels."""
+    if kind != "fw_pixel":
+        return None
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "fw_pixel_traffic.json")))
+        import hashlib
+        src = open(os.path.join(ROOT, "paper_1608_06192_gb300", "csrc", "fw.cu"), "rb").read()
+        if hashlib.sha1(src).hexdigest() != rec["fw_cu_sha1"]:
+            return None
+        return int(rec["dram_bytes_per_pixel"] * n)
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def algorithmic_bytes(kind, n, L, lat_m, lat_d, storage):
     """Bytes one Frank-Wolfe iteration must move for a kernel kind (all launches of it).
 
@@ -293,7 +310,7 @@ def main():
             ach = kinds[dom]["GB/s"]
             roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                     "frac": round(ach / hbm_peak, 4), "peak_source": peak_src,
-                    "bytes_per_launch": kinds[dom]["bytes_per_launch"], "traffic": None}
+                    "bytes_per_launch": kinds[dom]["bytes_per_launch"], "traffic": measured_traffic(dom, n)}
         launches = sum(c for c, _ in prof.values())
 
         # plain float32, one image, no batching
