@@ -34,11 +34,16 @@ namespace {
 // kF2 accumulates the gathered rows with packed two-wide FP32 FMAs.  (A
 // shared-memory hash aggregation of the splat was measured 2x slower than
 // plain FP32 reductions in L2: many pixels of a block hit the same key.)
-constexpr int kFix = 1, kF2 = 2;
-constexpr int kPixVariants = 7;
-constexpr int kPixPB[kPixVariants] = {256, 128, 256, 256, 128, 256, 256};
-constexpr int kPixMB[kPixVariants] = {4, 8, 4, 3, 6, 3, 4};
-constexpr int kPixMode[kPixVariants] = {0, 0, kFix, kFix, kFix, kFix | kF2, kFix | kF2};
+// kL3 is the label-split layout (three lanes per pixel, 80 pixels per block,
+// see pixel3).
+constexpr int kFix = 1, kF2 = 2, kL3 = 4;
+constexpr int kPixVariants = 8;
+constexpr int kPixPB[kPixVariants] = {256, 128, 256, 256, 128, 256, 256, 80};
+constexpr int kPixMB[kPixVariants] = {4, 8, 4, 3, 6, 3, 4, 0};
+constexpr int kPixMode[kPixVariants] = {0, 0, kFix, kFix, kFix, kFix | kF2, kFix | kF2, kL3};
+// chunk list of a pixel-block size (256, 128 or 80 pixels)
+constexpr int chunk_list(int pb) { return pb == 256 ? 0 : (pb == 128 ? 1 : 2); }
+constexpr int chunk_warps(int list) { return list == 0 ? 8 : (list == 1 ? 4 : 8); }
 constexpr int kVertBlock = 128;  // vertices per block
 constexpr int NS = 8;            // per-pixel scalar sums, see k_fw_pixel
 
@@ -128,7 +133,7 @@ struct PixArgs {
     int L;
     int Ls;                // shared-memory row stride (odd)
     bool y16;              // Y starts on a 16-byte boundary (lin always does)
-    float *cpart;          // [chunks][NS][2] per-chunk sums (hi, lo)
+    float *cpart;          // [chunks][PB / 32][NS] per-warp sums
     int *status;
 };
 
@@ -169,39 +174,18 @@ __device__ __forceinline__ void add_comp(float &hi, float &lo, float h2, float l
     lo += l2 + e;
 }
 
-// Sum over the block: FP32 within each warp, then across warps as a
-// compensated (hi, lo) pair; the block's N pairs are stored to
-// out[0 .. 2N) (one row of per-chunk partials, summed across chunks by the
-// step kernel).  No FP64 arithmetic here: the FP64 pipe of this part is
-// narrow, and the pairs keep the sums as accurate as FP64 across warps.
+// Per-warp FP32 sums of N values: lane 0 of warp w stores them to
+// out[w N .. w N + N) (one row of per-warp partials, summed across rows in
+// compensated FP32 by the step kernel).  No block barrier and no FP64 here.
 template <int N>
-__device__ __forceinline__ void block_sum_f32(float (&v)[N], float *out) {
-    __shared__ float red[32][N];
+__device__ __forceinline__ void warp_sums(float (&v)[N], float *out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < N; ++q) {
         float x = v[q];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0) red[warp][q] = x;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        const int nw = blockDim.x >> 5;
-#pragma unroll
-        for (int q = 0; q < N; ++q) {
-            float hi = lane < nw ? red[lane][q] : 0.f, lo = 0.f;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
-                const float l2 = __shfl_down_sync(0xffffffffu, lo, o);
-                add_comp(hi, lo, h2, l2);
-            }
-            if (lane == 0) {
-                out[2 * q] = hi;
-                out[2 * q + 1] = lo;
-            }
-        }
+        if (lane == 0) out[warp * N + q] = x;
     }
 }
 
@@ -458,6 +442,185 @@ __device__ __forceinline__ void pixel_chunk(const PixArgs &A, const FwLats &F, c
     }
 }
 
+// Label-split layout of the pixel pass (Lp = 24, Potts): three lanes per
+// pixel, lane q of a pixel owns labels 8q .. 8q+7, so one warp instruction
+// gathers ten whole 48-byte (FP16) corner rows instead of one 16-byte piece
+// of 32 different rows.  Lanes 30 and 31 of each warp are idle; a warp holds
+// ten pixels.  Same sums and splat as pixel_chunk: the per-pixel scalars
+// (total over labels, argmin) are combined over the three lanes in a fixed
+// order, so the lanes of a pixel agree bit for bit.
+constexpr int kL3Warps = 8;                 // warps per block
+constexpr int kL3Pixels = 10 * kL3Warps;    // pixels per block
+
+template <typename TB>
+__device__ __forceinline__ void pixel3(const PixArgs &A, const FwLats &F, const Chunk &ch, float *sy,
+                                       const float *sl, float (&part)[NS]) {
+    constexpr int LP = 24;
+    const int L = A.L;
+    const bool start = A.alpha == nullptr;
+    const float al = start ? 0.f : (float)A.alpha[ch.image];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) part[q] = 0.f;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane / 3, q = lane - 3 * (lane / 3);
+    const int px = 10 * warp + g;                        // pixel within the chunk
+    const bool valid = lane < 30 && px < ch.count;
+    const int64_t a = ch.begin + (valid ? px : 0);
+    const int base = 3 * (lane < 30 ? g : 9);            // first lane of this pixel's group
+    float *yw = sy + (valid ? px : 0) * A.Ls;
+    const float *lrow = sl + (valid ? px : 0) * A.Ls;
+    float ky[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) ky[j] = 0.f;
+    int sold = -1;
+    if (valid) {
+        if (!start) sold = A.s[a];
+        const bool fixed = F.nk == 2 && F.l[0].d1 == 6 && F.l[1].d1 == 3;
+        if (fixed) {
+            int v[9];
+            float w[9];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                v[k] = __ldg(F.l[0].pvid + a * 6 + k);
+                w[k] = __ldg(F.l[0].pbary + a * 6 + k) * F.l[0].ws0;
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                v[6 + k] = __ldg(F.l[1].pvid + a * 3 + k);
+                w[6 + k] = __ldg(F.l[1].pbary + a * 3 + k) * F.l[1].ws0;
+            }
+            const TB *s0p = slice_src<TB>(F.l[0]), *s1p = slice_src<TB>(F.l[1]);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const int vk = v[k] < 0 ? 0 : v[k];
+                const float wk = v[k] < 0 ? 0.f : w[k];
+                float o[8];
+                ld8(k < 6 ? s0p : s1p, vk, LP, q, o);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) ky[j] += wk * o[j];
+            }
+        } else {
+#pragma unroll
+            for (int mm = 0; mm < DCRF_MAX_KERNELS; ++mm) {
+                if (mm >= F.nk) break;
+                const FwLat &lt = F.l[mm];
+                const TB *src = slice_src<TB>(lt);
+                for (int k = 0; k < lt.d1; ++k) {
+                    const int v = __ldg(lt.pvid + a * lt.d1 + k);
+                    if (v < 0) continue;
+                    const float w = __ldg(lt.pbary + a * lt.d1 + k) * lt.ws0;
+                    float o[8];
+                    ld8(src, v, LP, q, o);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) ky[j] += w * o[j];
+                }
+            }
+        }
+        // y' over this lane's labels, written back to the shared row
+        if (!start) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int i = 8 * q + j;
+                if (i < L) {
+                    const float yv = yw[i];
+                    yw[i] = yv + al * ((i == sold ? 1.f : 0.f) - yv);
+                }
+            }
+        }
+    }
+    // totals over the pixel's labels: X = K~ y' - sum_w y', sum X, sum y'
+    float ptot = 0.f, psy = 0.f;
+    if (valid) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int i = 8 * q + j;
+            if (i < L) {
+                const float y = yw[i];
+                ky[j] -= A.sumw * y;
+                ptot += ky[j];
+                psy += y;
+            }
+        }
+    }
+    const float t0 = __shfl_sync(0xffffffffu, ptot, base), t1 = __shfl_sync(0xffffffffu, ptot, base + 1),
+                t2 = __shfl_sync(0xffffffffu, ptot, base + 2);
+    const float y0s = __shfl_sync(0xffffffffu, psy, base), y1s = __shfl_sync(0xffffffffu, psy, base + 1),
+                y2s = __shfl_sync(0xffffffffu, psy, base + 2);
+    const float tot = (t0 + t1) + t2, sy_ = (y0s + y1s) + y2s;
+    const float ca = valid ? A.c[a] : 0.f;
+    const float dpot = (float)(L - 1) * ca;
+    float best = INFINITY;
+    int sb = 0;
+    float lin_s = 0.f, P_s = 0.f, y_s = 0.f;
+    float s0 = 0.f, s1 = 0.f, s6 = 0.f, sp = 0.f;
+    if (valid) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int i = 8 * q + j;
+            if (i < L) {
+                const float y = yw[i];
+                const float P = (tot - ky[j]) + dpot * y;      // (Psi + D) y'
+                const float li = lrow[i];
+                const float gi = li + 2.f * P;
+                if (gi < best) { best = gi; sb = i; lin_s = li; P_s = P; y_s = y; }
+                s0 += li * y;
+                s1 += y * P;
+                s6 += dpot * y * y;
+                if (A.phi) sp += A.phi[a * L + i] * y;
+            }
+        }
+    }
+    // argmin over the three lanes (lowest label on ties: lane order is label order)
+    const float b0 = __shfl_sync(0xffffffffu, best, base), b1 = __shfl_sync(0xffffffffu, best, base + 1),
+                b2 = __shfl_sync(0xffffffffu, best, base + 2);
+    int win = 0;
+    float bw = b0;
+    if (b1 < bw) { bw = b1; win = 1; }
+    if (b2 < bw) { bw = b2; win = 2; }
+    const int sbw = __shfl_sync(0xffffffffu, sb, base + win);
+    if (valid) {
+        if (!(bw < INFINITY) && q == 0) dcrf_flag(A.status, DCRF_E_NONFINITE);
+        part[0] = s0;
+        part[1] = s1;
+        part[6] = s6;
+        part[7] = sp;
+        if (q == win) {
+            part[2] = lin_s;
+            part[3] = P_s;
+            part[4] = -A.sumw * (sy_ - y_s) + y_s * dpot;   // Potts: <y', mu e_s'> = sum y' - y'(s')
+            part[5] = dpot;                                  // mu(s', s') = 0
+        }
+        if (q == 0) A.s[a] = (uint8_t)sbw;
+        // splat of the one-hot s': lane q takes corners k = q, q + 3, ...
+#pragma unroll
+        for (int mm = 0; mm < DCRF_MAX_KERNELS; ++mm) {
+            if (mm >= F.nk) break;
+            const FwLat &lt = F.l[mm];
+            for (int k = q; k < lt.d1; k += 3) {
+                const int v = __ldg(lt.pvid + a * lt.d1 + k);
+                if (v >= 0) atomicAdd(lt.Slat + (int64_t)v * LP + sbw, __ldg(lt.pbary + a * lt.d1 + k));
+            }
+        }
+    }
+}
+
+template <typename TB>
+__global__ void __launch_bounds__(32 * kL3Warps) k_fw_pixel3(PixArgs A, FwLats F) {
+    extern __shared__ __align__(16) float smem[];
+    float *sy = smem;
+    float *sl = smem + kL3Pixels * A.Ls;
+    const Chunk ch = A.chunks[blockIdx.x];
+    tile_load_async(A, ch, sy, sl);
+    cp_commit();
+    cp_wait<0>();
+    __syncthreads();
+    float part[NS];
+    pixel3<TB>(A, F, ch, sy, sl, part);
+    __syncthreads();
+    if (A.alpha != nullptr) tile_store(A, ch, sy);
+    warp_sums<NS>(part, A.cpart + (int64_t)blockIdx.x * kL3Warps * NS);
+}
+
 // One block per chunk: the chunk's y and lin rows are copied to shared memory
 // (cp.async), every pixel is processed, y' is written back coalesced.
 template <int LP, typename TB, bool POTTS, int PB, int MB, int MODE>
@@ -474,7 +637,7 @@ __global__ void __launch_bounds__(PB, MB) k_fw_pixel(PixArgs A, FwLats F) {
     pixel_chunk<LP, TB, POTTS, MODE>(A, F, ch, sy, sl, part);
     __syncthreads();
     if (A.alpha != nullptr) tile_store(A, ch, sy);
-    block_sum_f32<NS>(part, A.cpart + (int64_t)blockIdx.x * 2 * NS);
+    warp_sums<NS>(part, A.cpart + (int64_t)blockIdx.x * (PB / 32) * NS);
 }
 
 // Blur pass `p` of every lattice in one launch (lattice m takes part while
@@ -600,13 +763,13 @@ __global__ void __launch_bounds__(256) k_fw_blur(BlurSet B, int p) {
 // Lattice dot products for the line search:
 //   0: w s0 sum_v sum_ij mu_ij Ylat[v][i] BS[v][j]   (= <y, K~-part of Psi s>)
 //   1: w s0 sum_v sum_ij mu_ij Slat[v][i] BS[v][j]   (= <s, K~-part of Psi s>)
-// summed per vertex chunk in FP32.
+// summed per warp in FP32.
 struct DotArgs {
     const Chunk *chunks;    // vertex chunks of lattice `which`
     const float *mu;
     int L;
     int which;
-    float *vpart;           // [vertex chunks of this lattice][2][2] per-chunk sums (hi, lo)
+    float *vpart;           // [vertex chunks of this lattice][warps][2] per-warp sums
 };
 
 template <int LP, typename T, bool POTTS>
@@ -648,33 +811,34 @@ __global__ void __launch_bounds__(kVertBlock) k_fw_latdot(DotArgs A, FwLat lt) {
         part[0] = lt.ws0 * py;
         part[1] = lt.ws0 * ps;
     }
-    block_sum_f32<2>(part, A.vpart + (int64_t)blockIdx.x * 4);
+    warp_sums<2>(part, A.vpart + (int64_t)blockIdx.x * (kVertBlock / 32) * 2);
 }
 
 // Per-image FP64 sums of per-chunk FP32 partials: chunks [range[b], range[b+1])
 // of rows of width W, summed into out[0 .. W) by the calling block.
 struct PartSums {
-    const float *cpart;                    // [pixel chunks][NS][2]
-    const int *crange;                     // [batch + 1]
-    const float *vpart;                    // [vertex chunks of all lattices][2][2]
-    const int *vrange;                     // [nk][batch + 1] into vpart rows
+    const float *cpart;                    // [pixel-chunk warps][NS]
+    const int *crange;                     // [batch + 1] rows of cpart per image
+    const float *vpart;                    // [vertex-chunk warps of all lattices][2]
+    const int *vrange;                     // [nk][batch + 1] rows of vpart per image
     int nk;
     int batch;
 };
 
-// Per-image sums of rows of W compensated (hi, lo) pairs, compensated FP32
+// Per-image sums of rows of W FP32 per-warp partials, compensated FP32
 // throughout (each thread's strided rows, warps, then across warps); each sum
 // becomes FP64 once, as hi + lo.  The result is valid in thread 0.
 template <int W>
-__device__ __forceinline__ void image_sums(const float *part, int c0, int c1, double (&out)[W]) {
+__device__ __forceinline__ void image_sums(const float *part, int r0, int r1, double (&out)[W]) {
     __shared__ float rh[32][W], rl[32][W];
     __shared__ double col[W];
     float hi[W], lo[W];
 #pragma unroll
     for (int q = 0; q < W; ++q) hi[q] = lo[q] = 0.f;
-    for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x)
+#pragma unroll 4
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x)
 #pragma unroll
-        for (int q = 0; q < W; ++q) add_comp(hi[q], lo[q], part[((int64_t)c * W + q) * 2], part[((int64_t)c * W + q) * 2 + 1]);
+        for (int q = 0; q < W; ++q) add_comp(hi[q], lo[q], part[(int64_t)r * W + q], 0.f);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < W; ++q) {
@@ -708,7 +872,7 @@ __device__ __forceinline__ void pixel_sums(const PartSums &P, int b, double (&sg
 
 // Step size and record of one iteration, one block per image; the last block
 // to finish advances the iteration counter.
-__global__ void k_fw_alpha(PartSums P, double *alpha, dcrf_fw_record *rec, int *counter, int *ticket,
+__global__ void __launch_bounds__(1024) k_fw_alpha(PartSums P, double *alpha, dcrf_fw_record *rec, int *counter, int *ticket,
                            int *status) {
     const int b = blockIdx.x;
     const int t = *counter;
@@ -796,7 +960,7 @@ __global__ void k_fw_lin(int64_t n, int L, const float *phi, const float *c, con
     lin[i] = p - scale * musum[l] * c[a] * yv;
 }
 
-__global__ void k_fw_qp_energy(PartSums P, double *out) {
+__global__ void __launch_bounds__(1024) k_fw_qp_energy(PartSums P, double *out) {
     double sg[NS];
     pixel_sums(P, blockIdx.x, sg);
     if (threadIdx.x == 0) out[blockIdx.x] = sg[7] + sg[1] - sg[6];   // phi^T y + y^T (Psi + D) y - y^T D y
@@ -815,8 +979,8 @@ struct Solver {
     float sumw = 0.f;
     const dcrf_lattice *lats = nullptr;
     FwLats F{};
-    Chunk *chunks_pb[2] = {nullptr, nullptr};   // 256- and 128-pixel chunk lists
-    int n_chunks_pb[2] = {0, 0};
+    Chunk *chunks_pb[3] = {nullptr, nullptr, nullptr};   // 256-, 128- and 80-pixel chunk lists
+    int n_chunks_pb[3] = {0, 0, 0};
     int variant = -1;                          // chosen pixel-kernel variant
     std::vector<Chunk *> vchunks;
     std::vector<int> n_vchunks;
@@ -825,7 +989,7 @@ struct Solver {
     float *cpart = nullptr, *vpart = nullptr;  // per-chunk FP32 partial sums
     int *crange = nullptr;                     // [2][batch + 1] pixel-chunk range per image
     int *vrange = nullptr;                     // [nk][batch + 1] vertex-chunk rows per image
-    std::vector<int64_t> voff;                 // first vpart row of each lattice
+    std::vector<int64_t> voff;                 // first vpart warp row of each lattice
     double *alpha = nullptr;
     int *counter = nullptr, *ticket = nullptr;
     dcrf_fw_record *rec = nullptr;
@@ -903,25 +1067,28 @@ struct Solver {
                 DCRF_TRY(cudaMemcpyAsync(chd, ch.data(), ch.size() * sizeof(Chunk), cudaMemcpyHostToDevice, s));
             vchunks.push_back(chd);
             n_vchunks.push_back((int)ch.size());
-            voff.push_back(m == 0 ? 0 : voff[m - 1] + n_vchunks[m - 1]);
+            constexpr int vw = kVertBlock / 32;   // warp rows per vertex chunk
+            voff.push_back(m == 0 ? 0 : voff[m - 1] + (int64_t)vw * n_vchunks[m - 1]);
             for (int b = 0; b <= batch; ++b) vrange_h.push_back((int)voff[m]);
-            for (const Chunk &c : ch) vrange_h[(size_t)m * (batch + 1) + c.image + 1]++;
+            for (const Chunk &c : ch) vrange_h[(size_t)m * (batch + 1) + c.image + 1] += vw;
             for (int b = 0; b < batch; ++b)
                 vrange_h[(size_t)m * (batch + 1) + b + 1] += vrange_h[(size_t)m * (batch + 1) + b] - (int)voff[m];
         }
-        std::vector<int> crange_h(2 * (batch + 1), 0);
-        for (int q = 0; q < 2; ++q) {
-            auto pc = make_chunks(lattices[0]->point_off, q == 0 ? 256 : 128);
+        std::vector<int> crange_h(3 * (batch + 1), 0);
+        for (int q = 0; q < 3; ++q) {
+            auto pc = make_chunks(lattices[0]->point_off, q == 0 ? 256 : (q == 1 ? 128 : kL3Pixels));
             n_chunks_pb[q] = (int)pc.size();
             DCRF_CHECK_STATUS(sc.get(&chunks_pb[q], pc.size() > 0 ? pc.size() : 1));
             if (!pc.empty())
                 DCRF_TRY(cudaMemcpyAsync(chunks_pb[q], pc.data(), pc.size() * sizeof(Chunk), cudaMemcpyHostToDevice, s));
-            for (const Chunk &c : pc) crange_h[q * (batch + 1) + c.image + 1]++;
+            for (const Chunk &c : pc) crange_h[q * (batch + 1) + c.image + 1] += chunk_warps(q);
             for (int b = 0; b < batch; ++b) crange_h[q * (batch + 1) + b + 1] += crange_h[q * (batch + 1) + b];
         }
-        const int64_t nv = nk > 0 ? voff[nk - 1] + n_vchunks[nk - 1] : 0;
-        DCRF_CHECK_STATUS(sc.get(&cpart, (size_t)std::max(1, std::max(n_chunks_pb[0], n_chunks_pb[1])) * NS * 2));
-        DCRF_CHECK_STATUS(sc.get(&vpart, (size_t)std::max<int64_t>(1, nv) * 4));
+        const int64_t nv = nk > 0 ? voff[nk - 1] + (int64_t)(kVertBlock / 32) * n_vchunks[nk - 1] : 0;
+        int64_t nrows = 1;
+        for (int q = 0; q < 3; ++q) nrows = std::max<int64_t>(nrows, (int64_t)chunk_warps(q) * n_chunks_pb[q]);
+        DCRF_CHECK_STATUS(sc.get(&cpart, (size_t)nrows * NS));
+        DCRF_CHECK_STATUS(sc.get(&vpart, (size_t)std::max<int64_t>(1, nv) * 2));
         DCRF_CHECK_STATUS(sc.get(&crange, crange_h.size()));
         DCRF_CHECK_STATUS(sc.get(&vrange, std::max<size_t>(1, vrange_h.size())));
         DCRF_TRY(cudaMemcpyAsync(crange, crange_h.data(), crange_h.size() * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -971,7 +1138,7 @@ struct Solver {
     // Partial-sum layout of the chosen pixel variant (after the first pixel pass).
     PartSums parts() const {
         PartSums P;
-        const int q = kPixPB[variant < 0 ? 0 : variant] == 256 ? 0 : 1;
+        const int q = chunk_list(kPixPB[variant < 0 ? 0 : variant]);
         P.cpart = cpart;
         P.crange = crange + q * (batch + 1);
         P.vpart = vpart;
@@ -984,7 +1151,7 @@ struct Solver {
     template <int LPc, typename T, bool POT, int PB, int MB, int MODE>
     dcrf_status pixel_v(float *Y, const float *phi, bool start, const double *alpha_override = nullptr) {
         PixArgs A;
-        const int q = PB == 256 ? 0 : 1;
+        const int q = chunk_list(PB);
         A.chunks = chunks_pb[q];
         A.alpha = start ? nullptr : (alpha_override ? alpha_override : alpha);
         A.Y = Y;
@@ -1001,15 +1168,24 @@ struct Solver {
         A.cpart = cpart;
         A.status = status;
         const size_t shm = 2 * (size_t)PB * Ls * sizeof(float);
-        auto kern = k_fw_pixel<LPc, T, POT, PB, MB, MODE>;
-        static bool attr = false;
-        if (!attr) {
+        void (*kern)(PixArgs, FwLats);
+        int threads = PB;
+        if constexpr ((MODE & kL3) != 0) {
+            static_assert(LPc == 24 && POT && PB == kL3Pixels, "label-split layout: 24 padded labels, Potts");
+            kern = k_fw_pixel3<T>;
+            threads = 32 * kL3Warps;
+        } else {
+            kern = k_fw_pixel<LPc, T, POT, PB, MB, MODE>;
+        }
+        // the row stride (and so the tile) grows with L: raise the limit when needed
+        static int attr_shm = 0;
+        if ((int)shm > attr_shm) {
             DCRF_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-            attr = true;
+            attr_shm = (int)shm;
         }
         if (n_chunks_pb[q] > 0) {
             ProfScope ps(P_FW_PIXEL, s);
-            kern<<<n_chunks_pb[q], PB, shm, s>>>(A, F);
+            kern<<<n_chunks_pb[q], threads, shm, s>>>(A, F);
             DCRF_LAUNCHED();
         }
         return DCRF_OK;
@@ -1029,6 +1205,7 @@ struct Solver {
                 DCRF_PIX_CASE(4);
                 DCRF_PIX_CASE(5);
                 DCRF_PIX_CASE(6);
+                DCRF_PIX_CASE(7);
             default: return pixel_v<LPc, T, POT, kPixPB[0], kPixMB[0], kPixMode[0]>(Y, phi, start, al);
             }
 #undef DCRF_PIX_CASE
@@ -1165,7 +1342,7 @@ struct Solver {
         A.mu = mu;
         A.L = L;
         A.which = which;
-        A.vpart = vpart + 4 * voff[which];
+        A.vpart = vpart + 2 * voff[which];
         if (n_vchunks[which] > 0) {
             ProfScope ps(P_FW_LATDOT, s);
             k_fw_latdot<LPc, T, POT><<<n_vchunks[which], kVertBlock, 0, s>>>(A, F.l[which]);
@@ -1193,7 +1370,7 @@ struct Solver {
         for (int m = 0; m < nk; ++m) DCRF_CHECK_STATUS(latdot(m));
         {
             ProfScope ps(P_FW_ALPHA, s);
-            k_fw_alpha<<<batch, 256, 0, s>>>(parts(), alpha, rec, counter, ticket, status);
+            k_fw_alpha<<<batch, 1024, 0, s>>>(parts(), alpha, rec, counter, ticket, status);
         }
         DCRF_LAUNCHED();
         const int G = Lp / 4;
@@ -1276,7 +1453,7 @@ extern "C" dcrf_status dcrf_dc_cccp(const float *unaries, const dcrf_lattice *la
     DCRF_CHECK_STATUS(S.sc.get(&qe, (size_t)(outer + 1) * S.batch));
     // S_QP at y^0
     DCRF_CHECK_STATUS(S.pixel(Y, unaries, true));
-    k_fw_qp_energy<<<S.batch, 256, 0, s>>>(S.parts(), qe);
+    k_fw_qp_energy<<<S.batch, 1024, 0, s>>>(S.parts(), qe);
     DCRF_LAUNCHED();
     const int G = S.Lp / 4;
     (void)G;
@@ -1289,7 +1466,7 @@ extern "C" dcrf_status dcrf_dc_cccp(const float *unaries, const dcrf_lattice *la
                                      (size_t)(S.F.l[m].m > 0 ? S.F.l[m].m : 1) * S.Lp * sizeof(float), s));
         DCRF_CHECK_STATUS(S.pixel(Y, inner == 0 ? unaries : nullptr, true));
         DCRF_CHECK_STATUS(S.run(Y, inner, unaries));
-        k_fw_qp_energy<<<S.batch, 256, 0, s>>>(S.parts(), qe + (int64_t)(o + 1) * S.batch);
+        k_fw_qp_energy<<<S.batch, 1024, 0, s>>>(S.parts(), qe + (int64_t)(o + 1) * S.batch);
         DCRF_LAUNCHED();
     }
     if (qp_energy) {

@@ -326,8 +326,9 @@ dcrf_status launch_project(const float *V, int64_t n, int L, const float *G, con
 // Its tagged vertices (node, vertex) go into a shared-memory hash table, the
 // right-child indicator is splatted, the d+1 Jacobi passes run between two
 // shared arrays, and the left-child points slice their sums into U.
-constexpr int kLocalP = 256;            // positions per block
-constexpr int kLocalSlots = 2048;       // hash slots (load <= 0.75 for d+1 <= 6)
+constexpr int kLocalP = 128;            // positions per block
+constexpr int kLocalBits = 11;
+constexpr int kLocalSlots = 1 << kLocalBits;   // hash slots (load <= 0.75 for d+1 <= 6)
 constexpr int kLocalThreads = 128;
 constexpr uint32_t kLocalEmpty = 0xFFFFFFFFu;
 constexpr int kLocalVertBits = 21;      // local vertex ids below 2^21
@@ -352,7 +353,7 @@ struct LocalArgs {
     float ws0;
 };
 
-__device__ __forceinline__ uint32_t local_hash(uint32_t k) { return (k * 0x9E3779B1u) >> (32 - 11); }
+__device__ __forceinline__ uint32_t local_hash(uint32_t k) { return (k * 0x9E3779B1u) >> (32 - kLocalBits); }
 
 __device__ __forceinline__ int local_insert(uint32_t *hkey, uint32_t key) {
     uint32_t h = local_hash(key);
