@@ -35,12 +35,15 @@ namespace {
 // shared-memory hash aggregation of the splat was measured 2x slower than
 // plain FP32 reductions in L2: many pixels of a block hit the same key.)
 // kL3 is the label-split layout (three lanes per pixel, 80 pixels per block,
-// see pixel3).
-constexpr int kFix = 1, kF2 = 2, kL3 = 4;
-constexpr int kPixVariants = 8;
-constexpr int kPixPB[kPixVariants] = {256, 128, 256, 256, 128, 256, 256, 80};
-constexpr int kPixMB[kPixVariants] = {4, 8, 4, 3, 6, 3, 4, 0};
-constexpr int kPixMode[kPixVariants] = {0, 0, kFix, kFix, kFix, kFix | kF2, kFix | kF2, kL3};
+// see pixel3); kEarly gathers the corner rows while the chunk's y and lin
+// rows are still in flight to shared memory.
+constexpr int kFix = 1, kF2 = 2, kL3 = 4, kEarly = 8;
+constexpr int kPixVariants = 10;
+constexpr int kPixPB[kPixVariants] = {256, 128, 256, 128, 256, 80, 128, 256, 128, 128};
+constexpr int kPixMB[kPixVariants] = {4, 8, 3, 6, 3, 0, 6, 3, 6, 8};
+constexpr int kPixMode[kPixVariants] = {0,           0,           kFix,         kFix,
+                                        kFix | kF2,  kL3,         kFix | kEarly, kFix | kEarly,
+                                        kFix | kF2 | kEarly, kFix | kEarly};
 // chunk list of a pixel-block size (256, 128 or 80 pixels)
 constexpr int chunk_list(int pb) { return pb == 256 ? 0 : (pb == 128 ? 1 : 2); }
 constexpr int chunk_warps(int list) { return list == 0 ? 8 : (list == 1 ? 4 : 8); }
@@ -317,12 +320,13 @@ __device__ __forceinline__ void pixel_chunk(const PixArgs &A, const FwLats &F, c
     const float *yrow = sy + t * A.Ls;
     const float *lrow = sl + t * A.Ls;
     int sb = 0;
-    if (valid) {
-        const int sold = start ? -1 : A.s[a];
-        // K~ y' gathered from the lattice, eight labels at a time
-        float ky[LP];
+    float ky[LP];
 #pragma unroll
-        for (int i = 0; i < LP; ++i) ky[i] = 0.f;
+    for (int i = 0; i < LP; ++i) ky[i] = 0.f;
+    int sold = -1;
+    if (valid) {
+        if (!start) sold = A.s[a];
+        // K~ y' gathered from the lattice, eight labels at a time
         constexpr bool F2 = (MODE & kF2) != 0;
         const bool fixed = (MODE & kFix) && F.nk == 2 && F.l[0].d1 == 6 && F.l[1].d1 == 3;
         if (fixed) gather_pair<LP, TB, 6, 3, F2>(F.l[0], F.l[1], a, ky);
@@ -343,6 +347,13 @@ __device__ __forceinline__ void pixel_chunk(const PixArgs &A, const FwLats &F, c
                 }
             }
         }
+    }
+    if constexpr ((MODE & kEarly) != 0) {
+        // the tile copies were left in flight during the gather
+        cp_wait<0>();
+        __syncthreads();
+    }
+    if (valid) {
         // y' = y + alpha (e_sold - y), written over the thread's shared-memory
         // row once (it is stored back to Y after the block)
         if (!start) {
@@ -631,8 +642,10 @@ __global__ void __launch_bounds__(PB, MB) k_fw_pixel(PixArgs A, FwLats F) {
     const Chunk ch = A.chunks[blockIdx.x];
     tile_load_async(A, ch, sy, sl);
     cp_commit();
-    cp_wait<0>();
-    __syncthreads();
+    if constexpr ((MODE & kEarly) == 0) {
+        cp_wait<0>();
+        __syncthreads();
+    }
     float part[NS];
     pixel_chunk<LP, TB, POTTS, MODE>(A, F, ch, sy, sl, part);
     __syncthreads();
@@ -1206,6 +1219,8 @@ struct Solver {
                 DCRF_PIX_CASE(5);
                 DCRF_PIX_CASE(6);
                 DCRF_PIX_CASE(7);
+                DCRF_PIX_CASE(8);
+                DCRF_PIX_CASE(9);
             default: return pixel_v<LPc, T, POT, kPixPB[0], kPixMB[0], kPixMode[0]>(Y, phi, start, al);
             }
 #undef DCRF_PIX_CASE

@@ -134,11 +134,11 @@ def test_fw_graph_path_matches_eager(dcrf):
     assert np.mean(d > 1e-4) <= 0.01
 
 
-@pytest.mark.parametrize("variant", range(8))
+@pytest.mark.parametrize("variant", range(10))
 def test_fw_every_pixel_variant(dcrf, variant, monkeypatch):
     # the autotuner chooses among these layouts of the pixel pass (block
-    # shapes, index prefetch, packed FMAs, three lanes per pixel); each must
-    # follow the oracle
+    # shapes, index prefetch, packed FMAs, three lanes per pixel, gather
+    # during the tile copy); each must follow the oracle
     monkeypatch.setenv("DCRF_PIXEL_VARIANT", str(variant))
     p = S.make_problem(96, 64, 8, 21, seed=13)
     for storage in ("f32", "f16"):
