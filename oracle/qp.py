@@ -20,6 +20,9 @@ operator; for a symmetric operator it equals the printed
 CCCP (Algorithm 2, Section 5.1): p(y) = phi^T y + y^T (Psi + D) y,
 q(y) = y^T D y; each outer step replaces the linear term by
 phi - grad q(y^t) = phi - 2 d o y^t and runs Frank-Wolfe warm-started at y^t.
+
+CCCP for negative semi-definite compatibilities (Section 5.2, Appendix C):
+one filter per outer step, then a per-pixel convex problem; see cccp_dc_neg.
 """
 from __future__ import annotations
 
@@ -72,6 +75,65 @@ def cccp_dc_gen(crf, y0, outer: int, inner: int):
         lin = crf.phi - 2.0 * crf.d * y
         y, P_y, _ = frank_wolfe(crf, y, inner, lin=lin, P_y=P_y)
         energies.append(s_qp(y, P_y))
+    return y, np.array(energies)
+
+
+# ---------------------------------------------------------------------------
+# CCCP on the DC relaxation for negative semi-definite compatibilities
+# (Section 5.2 and Appendix C).
+#
+# S_QP(y) = phi^T y + y^T Psi y with Psi = mu (x) (K - sum_w I) (reading c1)
+# splits into
+#   convex:   phi^T y - sum_w y^T (mu (x) I) y     (mu negative semi-definite on
+#                                                  the zero-sum directions of M)
+#   concave:  y^T (mu (x) K) y                     (K positive semi-definite)
+# Each outer step replaces the concave part by its linearisation at y^t, whose
+# gradient is (mu (x) K) y^t + (mu (x) K)^T y^t (exact for the evaluated,
+# slightly non-symmetric lattice operator; reading c4), and solves the convex
+# problem, which decouples over pixels (Appendix C):
+#   min_{y_a in simplex}  lin_a^T y_a - sum_w y_a^T mu y_a,
+#   lin_a = phi_a + mu (K y^t + K^T y^t)_a        (mu symmetric).
+# Potts (mu = 1 1^T - I): on the simplex - y^T mu y = |y|^2 - 1, so the
+# minimiser is the Euclidean projection of -lin_a / (2 sum_w) (closed form).
+# Other mu: `inner` Frank-Wolfe steps per pixel with the exact step of the
+# per-pixel quadratic, warm-started at y^t_a.
+
+
+def dc_neg_pixel_fw(lin, y0, mu, sum_w, inner: int):
+    """Frank-Wolfe on min lin_a^T y_a - sum_w y_a^T mu y_a for every pixel a."""
+    y = np.array(y0, dtype=np.float64)
+    rows = np.arange(y.shape[0])
+    for _ in range(inner):
+        g = lin - sum_w * (y @ (mu + mu.T))
+        s = np.zeros_like(y)
+        s[rows, np.argmin(g, axis=1)] = 1.0
+        d = s - y
+        A = -sum_w * np.einsum("ai,ij,aj->a", d, mu, d)
+        B = np.sum(g * d, axis=1)
+        al = np.array([step_size(a_, b_) for a_, b_ in zip(A, B)])
+        y = y + al[:, None] * d
+    return y
+
+
+def cccp_dc_neg(crf, y0, outer: int, inner: int = 0):
+    """Returns (y, qp_energies[outer+1]) with S_QP after every outer step."""
+    from oracle.lp import project_simplex
+    y = np.array(y0, dtype=np.float64)
+    mu = crf.mu
+    sw = crf.kernel.sum_w
+    potts = np.array_equal(mu, 1.0 - np.eye(crf.L))
+    energies = []
+    for t in range(outer + 1):
+        F = crf.kernel.apply(y) + crf.kernel.apply_T(y)          # K y + K^T y
+        # S_QP = phi^T y + 1/2 y^T mu F - sum_w y^T mu y  (y^T K y = y^T K^T y)
+        energies.append(float(np.sum(crf.phi * y) + 0.5 * np.sum(y * (F @ mu.T)) - sw * np.sum(y * (y @ mu.T))))
+        if t == outer:
+            break
+        lin = crf.phi + F @ mu.T
+        if potts:
+            y = project_simplex(-lin / (2.0 * sw))
+        else:
+            y = dc_neg_pixel_fw(lin, y, mu, sw, inner)
     return y, np.array(energies)
 
 
