@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-lp", action="store_true")
+    ap.add_argument("--no-dcneg", action="store_true")
     return ap.parse_args()
 
 
@@ -352,6 +353,28 @@ def main():
                   "ms_per_subgradient": round(lp_ms, 3), "subgradients_per_s": round(1000.0 / lp_ms, 2),
                   "label_levels_per_s": round(L * nlev * 1000.0 / lp_ms, 1)}
 
+        # CCCP for negative semi-definite compatibilities (Section 5.2) on the
+        # same batch: one filter (both blur directions) and one per-pixel
+        # projection per outer step
+        dcneg = None
+        if not args.no_dcneg:
+            outer = 10
+            Yn = torch.empty_like(y0)
+            Yn.copy_(y0)
+            D.dcrf_dc_neg(phi, [lb, ls], wts, Yn, 2, 0, storage=args.storage, energies=False, stream=stream)
+            stream.synchronize()
+            d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            Yn.copy_(y0)
+            d0.record(stream)
+            D.dcrf_dc_neg(phi, [lb, ls], wts, Yn, outer, 0, storage=args.storage, energies=False, stream=stream)
+            d1.record(stream)
+            stream.synchronize()
+            dn_ms = d0.elapsed_time(d1)
+            dcneg = {"workload": f"same batch ({B} x {W_}x{H_}), L=21, Potts, {args.storage} lattice storage, "
+                                 f"{outer} outer steps + the final energy",
+                     "ms_per_outer_step": round(dn_ms / (outer + 1), 3),
+                     "image_outer_steps_per_s": round(B * (outer + 1) / (dn_ms / 1000.0), 1)}
+
         # end to end through the public API from pinned host buffers
         e2e = None
         if not args.no_e2e:
@@ -408,6 +431,7 @@ def main():
                        "lattice_build_s": round(build_s, 4)},
             "plain_fp32_single_image": {"value": plain_fp32, "unit": UNIT},
             "lp_subgrad": lp,
+            "dc_neg": dcneg,
             "roofline": roof,
             "kernels": kinds,
             "cpu_baseline": cpu,

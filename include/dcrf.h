@@ -198,6 +198,25 @@ dcrf_status dcrf_dc_cccp(const float *unaries, const dcrf_lattice *lattices, con
                          double *qp_energy, int storage, dcrf_stream stream);
 
 /*
+ * CCCP on the DC relaxation for negative semi-definite compatibilities
+ * (Section 5.2, Appendix C).  S_QP(y) = [phi^T y - sum_w y^T (mu (x) I) y]
+ * + [y^T (mu (x) K~) y]; each of the `outer` steps filters y^t once (one
+ * splat, the forward and the reverse blur, one slice: F = K~ y + K~^T y) and
+ * solves the per-pixel problems min lin_a^T y_a - sum_w y_a^T mu y_a over the
+ * simplex with lin_a = phi_a + mu F_a: for Potts (compat NULL or 1 - I) the
+ * Euclidean projection of -lin_a / (2 sum_w); otherwise `inner` Frank-Wolfe
+ * steps per pixel with the exact step (compat must be symmetric; it should be
+ * negative semi-definite on zero-sum vectors for CCCP's monotone decrease).
+ * Y: device [N][L] on the simplex, updated in place.  qp_energy: host
+ * [outer+1][batch] or NULL: S_QP at the start and after every outer step
+ * (synchronises).  Errors: DCRF_E_INVAL for a bad argument, an asymmetric
+ * compat or sum_w = 0; DCRF_E_NONFINITE for non-finite data.
+ */
+dcrf_status dcrf_dc_neg(const float *unaries, const dcrf_lattice *lattices, const float *weights,
+                        int n_kernels, const float *compat, int L, int outer, int inner, float *Y,
+                        double *qp_energy, int storage, dcrf_stream stream);
+
+/*
  * LP relaxation subgradient (Eq. 18-20, Appendix D-E), Potts model.
  * For every label i the pixels are sorted by descending y_a(i) (ties by
  * ascending pixel index); the upper sums U_c = sum_{b after c} K~_cb come

@@ -56,6 +56,7 @@ _SIGS = {
     "dcrf_filter_static_capacity": ([], ctypes.c_size_t),
     "dcrf_qp_fw": ([_P, _P, _P, _I, _P, _I, _I, _P, _P, _I, _P], _I),
     "dcrf_dc_cccp": ([_P, _P, _P, _I, _P, _I, _I, _I, _P, _P, _I, _P], _I),
+    "dcrf_dc_neg": ([_P, _P, _P, _I, _P, _I, _I, _I, _P, _P, _I, _P], _I),
     "dcrf_qp_fw_backward": ([_P, _P, _P, _I, _P, _I, _I, _P, _P, _P, _P, _P, _P], _I),
     "dcrf_lp_subgrad": ([_P, _P, _P, _P, _I, _I, _P, _P, _P], _I),
     "dcrf_lp_solve": ([_P, _P, _P, _I, _I, _I, _D, _P, _P, _P], _I),
@@ -271,6 +272,25 @@ def dcrf_dc_cccp(unaries, lattices, weights, Y, outer: int, inner: int, compat=N
                               None if cm is None else cm[1], L, outer, inner, _ptr(Y),
                               None if qe is None else qe.ctypes.data_as(_P), STORAGE[storage],
                               _stream(stream)), "dcrf_dc_cccp")
+    return None if qe is None else qe.reshape(outer + 1, batch)
+
+
+def dcrf_dc_neg(unaries, lattices, weights, Y, outer: int, inner: int, compat=None, storage="f32",
+                 energies: bool = True, stream=None):
+    """CCCP for negative semi-definite mu (Section 5.2, Appendix C); Y updated in place.
+
+    Returns S_QP [outer+1, batch] or None.  `inner` is used for a non-Potts mu only.
+    """
+    unaries = _dev(unaries, torch.float32, "unaries", 2)
+    Y = _dev(Y, torch.float32, "Y", 2)
+    L = unaries.shape[1]
+    batch = lattices[0].batch
+    qe = np.zeros((outer + 1) * batch, dtype=np.float64) if energies else None
+    cm = _compat(compat, L)
+    _check(lib().dcrf_dc_neg(_ptr(unaries), _handles(lattices), _floats(weights), len(lattices),
+                             None if cm is None else cm[1], L, outer, inner, _ptr(Y),
+                             None if qe is None else qe.ctypes.data_as(_P), STORAGE[storage],
+                             _stream(stream)), "dcrf_dc_neg")
     return None if qe is None else qe.reshape(outer + 1, batch)
 
 

@@ -121,7 +121,7 @@ enum ProfId {
     P_EMBED = 0, P_FINALIZE, P_NEIGHBOURS, P_SPLAT_DENSE, P_BLUR, P_SLICE,
     P_FW_PIXEL, P_FW_LATDOT, P_FW_ALPHA, P_FW_LATUPD, P_FW_LIN,
     P_LP_SORT, P_LP_RUNS, P_LP_SPLAT, P_LP_NEIGHBOURS, P_LP_BLUR, P_LP_SLICE, P_LP_COMBINE,
-    P_LP_PROJECT, P_LP_LOCAL, P_FW_BLUR
+    P_LP_PROJECT, P_LP_LOCAL, P_FW_BLUR, P_DCNEG_PIXEL
 };
 struct ProfScope {
     ProfScope(int id, cudaStream_t s);

@@ -1495,6 +1495,358 @@ extern "C" dcrf_status dcrf_dc_cccp(const float *unaries, const dcrf_lattice *la
     return DCRF_OK;
 }
 
+namespace {
+
+// ---------------------------------------------------------------------------
+// CCCP for negative semi-definite compatibilities (Section 5.2, Appendix C).
+//
+// S_QP(y) = [phi^T y - sum_w y^T (mu (x) I) y] + [y^T (mu (x) K~) y]: convex
+// plus concave on M.  Each outer step needs one filter of y^t: the gradient
+// of the concave part is mu (K~ y + K~^T y), and since K~ = S^T B S and
+// K~^T = S^T B^T S (B^T: the blur axes in reverse order), one splat of y feeds
+// the forward and the reverse blur and a single slice of their sum.  The
+// convex problem then decouples over pixels:
+//   min_{y_a in simplex} lin_a^T y_a - sum_w y_a^T mu y_a,
+//   lin_a = phi_a + mu (K~ y^t + K~^T y^t)_a.
+// Potts: the minimiser is the Euclidean projection of -lin_a / (2 sum_w)
+// (Michelot's active-set iteration); other symmetric mu: `inner` per-pixel
+// Frank-Wolfe steps with the exact step, from y^t_a.  The same pass sums
+// S_QP(y^t) = phi^T y + 1/2 y^T mu F - sum_w y^T mu y, F = K~ y + K~^T y.
+
+struct NegLat {
+    const int32_t *pvid;
+    const float *pbary;
+    const void *V1;    // [m][Lp] B S y   (storage type)
+    const void *V2;    // [m][Lp] B^T S y (storage type)
+    int d1;
+    float ws0;
+};
+
+struct NegArgs {
+    const Chunk *chunks;   // 256-pixel chunks
+    NegLat l[DCRF_MAX_KERNELS];
+    int nk;
+    float *Y;              // [n][L] in/out
+    const float *phi;      // [n][L]
+    const float *mu;       // [L][L] (general mu)
+    int L;
+    int inner;
+    bool update;           // false: energy only
+    float sumw;
+    float *epart;          // [chunks][8 warps] per-warp S_QP sums
+    int *status;
+};
+
+template <int LP, typename TB, bool POTTS>
+__global__ void __launch_bounds__(256) k_dcneg_pixel(NegArgs A) {
+    const Chunk ch = A.chunks[blockIdx.x];
+    const int t = threadIdx.x;
+    const bool valid = t < ch.count;
+    const int64_t a = ch.begin + (valid ? t : 0);
+    const int L = A.L;
+    float e = 0.f;
+    if (valid) {
+        // F = sum_m w_m s0_m S_m^T (B_m + B_m^T) S_m y, eight labels at a time
+        float F[LP];
+#pragma unroll
+        for (int i = 0; i < LP; ++i) F[i] = 0.f;
+#pragma unroll
+        for (int mm = 0; mm < DCRF_MAX_KERNELS; ++mm) {
+            if (mm >= A.nk) break;
+            const NegLat &lt = A.l[mm];
+            for (int k = 0; k < lt.d1; ++k) {
+                const int v = __ldg(lt.pvid + a * lt.d1 + k);
+                if (v < 0) continue;
+                const float w = __ldg(lt.pbary + a * lt.d1 + k) * lt.ws0;
+#pragma unroll
+                for (int h = 0; h < LP / 8; ++h) {
+                    float o1[8], o2[8];
+                    ld8((const TB *)lt.V1, v, LP, h, o1);
+                    ld8((const TB *)lt.V2, v, LP, h, o2);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) F[8 * h + j] += w * (o1[j] + o2[j]);
+                }
+            }
+        }
+        float y[LP], ph[LP], muF[LP], muy[LP];
+#pragma unroll
+        for (int i = 0; i < LP; ++i) {
+            y[i] = i < L ? A.Y[a * L + i] : 0.f;
+            ph[i] = i < L ? A.phi[a * L + i] : 0.f;
+        }
+        if (POTTS) {
+            float tF = 0.f, ty = 0.f;
+#pragma unroll
+            for (int i = 0; i < LP; ++i)
+                if (i < L) { tF += F[i]; ty += y[i]; }
+#pragma unroll
+            for (int i = 0; i < LP; ++i) {
+                muF[i] = tF - F[i];
+                muy[i] = ty - y[i];
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < LP; ++i) {
+                float sf = 0.f, sy = 0.f;
+                if (i < L) {
+#pragma unroll 8
+                    for (int j = 0; j < LP; ++j)
+                        if (j < L) {
+                            const float m = A.mu[i * L + j];
+                            sf += m * F[j];
+                            sy += m * y[j];
+                        }
+                }
+                muF[i] = sf;
+                muy[i] = sy;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < LP; ++i)
+            if (i < L) e += ph[i] * y[i] + 0.5f * y[i] * muF[i] - A.sumw * y[i] * muy[i];
+        if (A.update) {
+            float lin[LP];
+#pragma unroll
+            for (int i = 0; i < LP; ++i) lin[i] = ph[i] + muF[i];
+            if (POTTS) {
+                // projection of v = -lin / (2 sum_w) onto the simplex; the
+                // projection is unchanged by a shift of v, and shifting by
+                // max v keeps tau small so that v - tau does not cancel
+                const float sc = -0.5f / A.sumw;
+                float v[LP];
+                bool act[LP];
+                float vmax = -INFINITY;
+#pragma unroll
+                for (int i = 0; i < LP; ++i) {
+                    v[i] = lin[i] * sc;
+                    act[i] = i < L;
+                    if (i < L) {
+                        if (!isfinite(v[i])) dcrf_flag(A.status, DCRF_E_NONFINITE);
+                        vmax = fmaxf(vmax, v[i]);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < LP; ++i) v[i] -= vmax;
+                float tau = 0.f;
+                for (int it = 0; it <= L; ++it) {
+                    float sm = 0.f;
+                    int cnt = 0;
+#pragma unroll
+                    for (int i = 0; i < LP; ++i)
+                        if (act[i]) { sm += v[i]; ++cnt; }
+                    tau = (sm - 1.f) / (float)cnt;
+                    bool changed = false;
+#pragma unroll
+                    for (int i = 0; i < LP; ++i)
+                        if (act[i] && v[i] <= tau) { act[i] = false; changed = true; }
+                    if (!changed) break;
+                }
+#pragma unroll
+                for (int i = 0; i < LP; ++i) y[i] = act[i] ? v[i] - tau : 0.f;
+            } else {
+                // Frank-Wolfe on lin^T y - sum_w y^T mu y (mu symmetric): gradient
+                // lin - 2 sum_w mu y, exact step on the per-pixel quadratic
+                for (int it = 0; it < A.inner; ++it) {
+                    float g[LP];
+                    float best = INFINITY;
+                    int sb = 0;
+#pragma unroll
+                    for (int i = 0; i < LP; ++i) {
+                        g[i] = lin[i] - 2.f * A.sumw * muy[i];
+                        if (i < L && g[i] < best) { best = g[i]; sb = i; }
+                    }
+                    if (!(best < INFINITY)) { dcrf_flag(A.status, DCRF_E_NONFINITE); break; }
+                    // d = e_sb - y:  d^T mu d = mu_ss - 2 (mu y)_s + y^T mu y,  g^T d = g_s - g^T y
+                    float ymy = 0.f, gy = 0.f;
+#pragma unroll
+                    for (int i = 0; i < LP; ++i)
+                        if (i < L) { ymy += y[i] * muy[i]; gy += g[i] * y[i]; }
+                    float muys = 0.f, gs = 0.f;
+#pragma unroll
+                    for (int i = 0; i < LP; ++i)
+                        if (i == sb) { muys = muy[i]; gs = g[i]; }
+                    const float dmd = A.mu[sb * L + sb] - 2.f * muys + ymy;
+                    const float qa = -A.sumw * dmd, qb = gs - gy;
+                    float al;
+                    if (qa > 0.f) al = fminf(1.f, fmaxf(0.f, -qb / (2.f * qa)));
+                    else al = (qa + qb < 0.f) ? 1.f : 0.f;
+                    // y += al (e_s - y); mu y += al (mu e_s - mu y)
+#pragma unroll
+                    for (int i = 0; i < LP; ++i) {
+                        if (i < L) {
+                            y[i] += al * ((i == sb ? 1.f : 0.f) - y[i]);
+                            muy[i] += al * (A.mu[i * L + sb] - muy[i]);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < LP; ++i)
+                if (i < L) A.Y[a * L + i] = y[i];
+        }
+    }
+    float part[1] = {e};
+    warp_sums<1>(part, A.epart + (int64_t)blockIdx.x * 8);
+}
+
+// S_QP per image from the per-warp rows (compensated FP32, FP64 once).
+__global__ void __launch_bounds__(1024) k_dcneg_energy(const float *epart, const int *crange, double *out) {
+    double e[1];
+    image_sums<1>(epart, crange[blockIdx.x], crange[blockIdx.x + 1], e);
+    if (threadIdx.x == 0) out[blockIdx.x] = e[0];
+}
+
+struct NegSolver {
+    cudaStream_t s;
+    Scratch sc;
+    int L = 0, Lp = 0, batch = 0, storage = 0, nk = 0;
+    int64_t n = 0;
+    bool potts = true;
+    float sumw = 0.f;
+    const dcrf_lattice *lats = nullptr;
+    float *V[DCRF_MAX_KERNELS] = {};
+    void *V1[DCRF_MAX_KERNELS] = {}, *V2[DCRF_MAX_KERNELS] = {}, *tmp[DCRF_MAX_KERNELS] = {};
+    float *mu = nullptr, *epart = nullptr;
+    int *crange = nullptr;
+    Chunk *chunks = nullptr;
+    int n_chunks = 0;
+    NegArgs A{};
+
+    explicit NegSolver(cudaStream_t st) : s(st), sc(st) {}
+
+    dcrf_status setup(const float *unaries, const dcrf_lattice *lattices, const float *weights, int n_k,
+                      const float *compat, int L_, int store, float *Y, int inner) {
+        DCRF_CHECK_STATUS(dcrf_check_lattices(lattices, n_k));
+        if (!unaries || !weights || !Y || L_ < 1 || L_ > DCRF_MAX_L || inner < 0) return DCRF_E_INVAL;
+        if (store != DCRF_STORAGE_F32 && store != DCRF_STORAGE_F16) return DCRF_E_INVAL;
+        lats = lattices;
+        nk = n_k;
+        L = L_;
+        Lp = L <= 8 ? 8 : (L <= 24 ? 24 : 64);
+        storage = store;
+        n = lattices[0]->n;
+        batch = lattices[0]->batch;
+        sumw = 0.f;
+        for (int m = 0; m < nk; ++m) {
+            if (!(weights[m] >= 0.f)) return DCRF_E_INVAL;
+            sumw += weights[m];
+        }
+        if (!(sumw > 0.f)) return DCRF_E_INVAL;
+        potts = true;
+        std::vector<float> mu_h(L * L);
+        for (int i = 0; i < L; ++i)
+            for (int j = 0; j < L; ++j) {
+                const float v = compat ? compat[i * L + j] : (i == j ? 0.f : 1.f);
+                if (!std::isfinite(v)) return DCRF_E_INVAL;
+                mu_h[i * L + j] = v;
+                if (v != (i == j ? 0.f : 1.f)) potts = false;
+            }
+        for (int i = 0; i < L; ++i)
+            for (int j = 0; j < i; ++j)
+                if (mu_h[i * L + j] != mu_h[j * L + i]) return DCRF_E_INVAL;   // mu must be symmetric
+        DCRF_CHECK_STATUS(sc.get(&mu, (size_t)L * L));
+        DCRF_TRY(cudaMemcpyAsync(mu, mu_h.data(), L * L * sizeof(float), cudaMemcpyHostToDevice, s));
+        const size_t esz = storage == DCRF_STORAGE_F16 ? 2 : 4;
+        A.nk = nk;
+        for (int m = 0; m < nk; ++m) {
+            const dcrf_lattice lat = lattices[m];
+            const size_t cnt = (size_t)(lat->m > 0 ? lat->m : 1) * Lp;
+            char *b1, *b2, *bt;
+            DCRF_CHECK_STATUS(sc.get(&V[m], cnt));
+            DCRF_CHECK_STATUS(sc.get(&b1, cnt * esz));
+            DCRF_CHECK_STATUS(sc.get(&b2, cnt * esz));
+            DCRF_CHECK_STATUS(sc.get(&bt, cnt * esz));
+            V1[m] = b1;
+            V2[m] = b2;
+            tmp[m] = bt;
+            A.l[m].pvid = lat->pvid;
+            A.l[m].pbary = lat->pbary;
+            A.l[m].V1 = b1;
+            A.l[m].V2 = b2;
+            A.l[m].d1 = lat->d + 1;
+            A.l[m].ws0 = (float)(weights[m] * lat->s0);
+        }
+        auto pc = make_chunks(lattices[0]->point_off, 256);
+        n_chunks = (int)pc.size();
+        DCRF_CHECK_STATUS(sc.get(&chunks, pc.size() > 0 ? pc.size() : 1));
+        if (!pc.empty())
+            DCRF_TRY(cudaMemcpyAsync(chunks, pc.data(), pc.size() * sizeof(Chunk), cudaMemcpyHostToDevice, s));
+        std::vector<int> cr(batch + 1, 0);
+        for (const Chunk &c : pc) cr[c.image + 1] += 8;
+        for (int b = 0; b < batch; ++b) cr[b + 1] += cr[b];
+        DCRF_CHECK_STATUS(sc.get(&crange, (size_t)batch + 1));
+        DCRF_TRY(cudaMemcpyAsync(crange, cr.data(), (batch + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+        DCRF_CHECK_STATUS(sc.get(&epart, (size_t)std::max(1, n_chunks) * 8));
+        A.chunks = chunks;
+        A.Y = Y;
+        A.phi = unaries;
+        A.mu = mu;
+        A.L = L;
+        A.inner = inner;
+        A.sumw = sumw;
+        A.epart = epart;
+        A.status = lattices[0]->status;
+        return DCRF_OK;
+    }
+
+    // F = (K~ + K~^T) y per lattice (splat once, blur both ways), then the
+    // per-pixel pass; energy of the current y into out[batch] (device).
+    dcrf_status step(bool update, double *out) {
+        for (int m = 0; m < nk; ++m) {
+            const dcrf_lattice lat = lats[m];
+            const size_t cnt = (size_t)(lat->m > 0 ? lat->m : 1) * Lp;
+            DCRF_TRY(cudaMemsetAsync(V[m], 0, cnt * sizeof(float), s));
+            DCRF_CHECK_STATUS(dcrf_splat_dense(lat, A.Y, L, V[m], Lp, s));
+            DCRF_CHECK_STATUS(dcrf_blur(lat, V[m], V1[m], tmp[m], Lp, storage, false, s));
+            DCRF_CHECK_STATUS(dcrf_blur(lat, V[m], V2[m], tmp[m], Lp, storage, true, s));
+        }
+        A.update = update;
+        if (n_chunks > 0) {
+            ProfScope ps(P_DCNEG_PIXEL, s);
+            const bool h = storage == DCRF_STORAGE_F16;
+#define DCRF_NEG(LPc) \
+    do { \
+        if (h) { if (potts) k_dcneg_pixel<LPc, __half, true><<<n_chunks, 256, 0, s>>>(A); \
+                 else k_dcneg_pixel<LPc, __half, false><<<n_chunks, 256, 0, s>>>(A); } \
+        else { if (potts) k_dcneg_pixel<LPc, float, true><<<n_chunks, 256, 0, s>>>(A); \
+               else k_dcneg_pixel<LPc, float, false><<<n_chunks, 256, 0, s>>>(A); } \
+    } while (0)
+            if (Lp == 8) DCRF_NEG(8);
+            else if (Lp == 24) DCRF_NEG(24);
+            else DCRF_NEG(64);
+#undef DCRF_NEG
+            DCRF_LAUNCHED();
+        }
+        k_dcneg_energy<<<batch, 1024, 0, s>>>(epart, crange, out);
+        DCRF_LAUNCHED();
+        return DCRF_OK;
+    }
+};
+
+}  // namespace
+
+extern "C" dcrf_status dcrf_dc_neg(const float *unaries, const dcrf_lattice *lattices, const float *weights,
+                                   int n_kernels, const float *compat, int L, int outer, int inner, float *Y,
+                                   double *qp_energy, int storage, dcrf_stream stream) {
+    if (outer < 0 || inner < 0) return DCRF_E_INVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    NegSolver S(s);
+    DCRF_CHECK_STATUS(S.setup(unaries, lattices, weights, n_kernels, compat, L, storage, Y, inner));
+    if (S.n == 0) return DCRF_OK;
+    double *qe;
+    DCRF_CHECK_STATUS(S.sc.get(&qe, (size_t)(outer + 1) * S.batch));
+    for (int t = 0; t <= outer; ++t) DCRF_CHECK_STATUS(S.step(t < outer, qe + (int64_t)t * S.batch));
+    if (qp_energy) {
+        DCRF_TRY(cudaMemcpyAsync(qp_energy, qe, (size_t)(outer + 1) * S.batch * sizeof(double),
+                                 cudaMemcpyDeviceToHost, s));
+        int h = 0;
+        DCRF_TRY(cudaMemcpyAsync(&h, lattices[0]->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        DCRF_TRY(cudaStreamSynchronize(s));
+        if (h != 0) return (dcrf_status)h;
+    }
+    return DCRF_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Reverse mode through unrolled Frank-Wolfe.
 //

@@ -286,11 +286,17 @@ __global__ void k_project(const float *__restrict__ V, int64_t n, int L, const f
     }
     float v[LP];
     bool act[LP];
+    float vmax = -INFINITY;
 #pragma unroll
     for (int i = 0; i < LP; ++i) {
         v[i] = i < L ? V[a * L + i] - (G ? beta * G[a * L + i] : 0.f) : 0.f;
         act[i] = i < L;
+        if (i < L) vmax = fmaxf(vmax, v[i]);
     }
+    // the projection is unchanged by a shift of v; shifting by max v keeps
+    // tau small, so that v - tau does not cancel for large inputs
+#pragma unroll
+    for (int i = 0; i < LP; ++i) v[i] -= vmax;
     float tau = 0.f;
     for (int it = 0; it <= L; ++it) {
         float s = 0.f;
