@@ -181,15 +181,15 @@ class ClockSampler:
 
 def measured_traffic(kind, n):
     """DRAM bytes per launch of the pixel kernel from the committed ncu capture
-    (profiles/fw_pixel_traffic.json), scaled by pixels; None when the kernel
-    source changed since the capture or for other kernels."""
+    (profiles/fw_pixel_traffic.json), scaled by pixels; None when the kernel's
+    source (csrc/fw_pixel.cuh) changed since the capture, or for other kernels."""
     if kind != "fw_pixel":
         return None
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "fw_pixel_traffic.json")))
         import hashlib
-        src = open(os.path.join(ROOT, "paper_1608_06192_gb300", "csrc", "fw.cu"), "rb").read()
-        if hashlib.sha1(src).hexdigest() != rec["fw_cu_sha1"]:
+        src = open(os.path.join(ROOT, "paper_1608_06192_gb300", "csrc", "fw_pixel.cuh"), "rb").read()
+        if hashlib.sha1(src).hexdigest() != rec["source_sha1"]:
             return None
         return int(rec["dram_bytes_per_pixel"] * n)
     except (OSError, KeyError, ValueError):

@@ -217,6 +217,37 @@ dcrf_status dcrf_dc_neg(const float *unaries, const dcrf_lattice *lattices, cons
                         double *qp_energy, int storage, dcrf_stream stream);
 
 /*
+ * Parallel mean field, the baseline the paper compares with (Section 1,
+ * Section 6.2: MF, and MF5 = 5 iterations), for P(x) proportional to
+ * exp(-E(x)) with E of Eq. 1 (ordered pairs):
+ *   Q <- softmax_rows(-phi - (Psi + Psi^T) Q),  Psi = mu (x) (K~ - sum_w I),
+ * one filter per iteration (one splat, the forward and the reverse blur, one
+ * slice).  Q: device [N][L], rows on the simplex (e.g. softmax(-phi)), updated
+ * in place.  qp_energy: host [iters+1][batch] or NULL: S_QP(Q) = phi^T Q +
+ * Q^T Psi Q before every update and at the end (synchronises).  compat must
+ * be symmetric (NULL: Potts).
+ */
+dcrf_status dcrf_mean_field(const float *unaries, const dcrf_lattice *lattices, const float *weights,
+                            int n_kernels, const float *compat, int L, int iters, float *Q,
+                            double *qp_energy, int storage, dcrf_stream stream);
+
+/*
+ * Rounding of a relaxed solution: labels[a] = argmax_i Y[a][i] (lowest label
+ * on ties), int32 device [N]; onehot: device [N][L] or NULL.  Asynchronous.
+ */
+dcrf_status dcrf_round(const float *Y, int64_t n, int L, int32_t *labels, float *onehot, dcrf_stream stream);
+
+/*
+ * Energy of a labelling, Eq. 1 (ordered pairs, pixel operator through the
+ * lattices): E(x) = S_QP at the one-hot rows of x.  labels: device int32 [N]
+ * in [0, L) (else DCRF_E_INVAL); energy: host [batch] (synchronises).
+ * compat must be symmetric (NULL: Potts).
+ */
+dcrf_status dcrf_labelling_energy(const float *unaries, const dcrf_lattice *lattices, const float *weights,
+                                  int n_kernels, const float *compat, int L, const int32_t *labels,
+                                  double *energy, int storage, dcrf_stream stream);
+
+/*
  * LP relaxation subgradient (Eq. 18-20, Appendix D-E), Potts model.
  * For every label i the pixels are sorted by descending y_a(i) (ties by
  * ascending pixel index); the upper sums U_c = sum_{b after c} K~_cb come

@@ -57,6 +57,9 @@ _SIGS = {
     "dcrf_qp_fw": ([_P, _P, _P, _I, _P, _I, _I, _P, _P, _I, _P], _I),
     "dcrf_dc_cccp": ([_P, _P, _P, _I, _P, _I, _I, _I, _P, _P, _I, _P], _I),
     "dcrf_dc_neg": ([_P, _P, _P, _I, _P, _I, _I, _I, _P, _P, _I, _P], _I),
+    "dcrf_mean_field": ([_P, _P, _P, _I, _P, _I, _I, _P, _P, _I, _P], _I),
+    "dcrf_round": ([_P, ctypes.c_int64, _I, _P, _P, _P], _I),
+    "dcrf_labelling_energy": ([_P, _P, _P, _I, _P, _I, _P, _P, _I, _P], _I),
     "dcrf_qp_fw_backward": ([_P, _P, _P, _I, _P, _I, _I, _P, _P, _P, _P, _P, _P], _I),
     "dcrf_lp_subgrad": ([_P, _P, _P, _P, _I, _I, _P, _P, _P], _I),
     "dcrf_lp_solve": ([_P, _P, _P, _I, _I, _I, _D, _P, _P, _P], _I),
@@ -292,6 +295,46 @@ def dcrf_dc_neg(unaries, lattices, weights, Y, outer: int, inner: int, compat=No
                              None if qe is None else qe.ctypes.data_as(_P), STORAGE[storage],
                              _stream(stream)), "dcrf_dc_neg")
     return None if qe is None else qe.reshape(outer + 1, batch)
+
+
+def dcrf_mean_field(unaries, lattices, weights, Q, iters: int, compat=None, storage="f32", energies: bool = True,
+                    stream=None):
+    """Parallel mean field (the MF baseline); Q updated in place.  Returns S_QP [iters+1, batch] or None."""
+    unaries = _dev(unaries, torch.float32, "unaries", 2)
+    Q = _dev(Q, torch.float32, "Q", 2)
+    L = unaries.shape[1]
+    batch = lattices[0].batch
+    qe = np.zeros((iters + 1) * batch, dtype=np.float64) if energies else None
+    cm = _compat(compat, L)
+    _check(lib().dcrf_mean_field(_ptr(unaries), _handles(lattices), _floats(weights), len(lattices),
+                                 None if cm is None else cm[1], L, iters, _ptr(Q),
+                                 None if qe is None else qe.ctypes.data_as(_P), STORAGE[storage],
+                                 _stream(stream)), "dcrf_mean_field")
+    return None if qe is None else qe.reshape(iters + 1, batch)
+
+
+def dcrf_round(Y, onehot: bool = False, stream=None):
+    """Most probable label per pixel (int32), and the one-hot rows when asked."""
+    Y = _dev(Y, torch.float32, "Y", 2)
+    labels = torch.empty(Y.shape[0], dtype=torch.int32, device=Y.device)
+    oh = torch.empty_like(Y) if onehot else None
+    _check(lib().dcrf_round(_ptr(Y), Y.shape[0], Y.shape[1], _ptr(labels), None if oh is None else _ptr(oh),
+                            _stream(stream)), "dcrf_round")
+    return (labels, oh) if onehot else labels
+
+
+def dcrf_labelling_energy(unaries, lattices, weights, labels, compat=None, storage="f32", stream=None):
+    """E(x) of Eq. 1 per image (host float64 [batch])."""
+    unaries = _dev(unaries, torch.float32, "unaries", 2)
+    labels = _dev(labels, torch.int32, "labels", 1)
+    L = unaries.shape[1]
+    out = np.zeros(lattices[0].batch, dtype=np.float64)
+    cm = _compat(compat, L)
+    _check(lib().dcrf_labelling_energy(_ptr(unaries), _handles(lattices), _floats(weights), len(lattices),
+                                       None if cm is None else cm[1], L, _ptr(labels),
+                                       out.ctypes.data_as(_P), STORAGE[storage], _stream(stream)),
+           "dcrf_labelling_energy")
+    return out
 
 
 def dcrf_lp_subgrad(unaries, Y, lattices, weights, energy: bool = True, stream=None):
