@@ -387,6 +387,8 @@ __global__ void __launch_bounds__(kLocalThreads) k_lp_local(LocalArgs A) {
     uint32_t *hkey = lsm;
     float *val = reinterpret_cast<float *>(lsm + kLocalSlots);
     float *tmp = val + kLocalSlots;
+    uint16_t *occ = reinterpret_cast<uint16_t *>(tmp + kLocalSlots);   // occupied slots, compacted
+    __shared__ int wsum[kLocalThreads / 32];
     const LocalBlock blk = A.blocks[blockIdx.x];
     const int b = blk.image;
     const int64_t off = A.point_off[b];
@@ -432,16 +434,45 @@ __global__ void __launch_bounds__(kLocalThreads) k_lp_local(LocalArgs A) {
         }
     }
     __syncthreads();
-    // d+1 Jacobi passes along w_j, absent neighbours read as 0; eight slots per
-    // thread per step so that their neighbour-table loads are in flight together
+    // compact the occupied slots (thread t scans slots [t S, t S + S) in order;
+    // block-wide exclusive scan of the counts): the passes visit only those
+    constexpr int kPer = kLocalSlots / kLocalThreads;
+    int mine = 0;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) mine += hkey[threadIdx.x * kPer + i] != kLocalEmpty;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int x = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += x;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    int base = incl - mine, nocc = 0;
+#pragma unroll
+    for (int w = 0; w < kLocalThreads / 32; ++w) {
+        if (w < wid) base += wsum[w];
+        nocc += wsum[w];
+    }
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const int slot = threadIdx.x * kPer + i;
+        if (hkey[slot] != kLocalEmpty) occ[base++] = (uint16_t)slot;
+    }
+    __syncthreads();
+    // d+1 Jacobi passes along w_j over the occupied slots, absent neighbours
+    // read as 0; eight slots per thread per step so that their neighbour-table
+    // loads are in flight together
     for (int j = 0; j < A.d1; ++j) {
-        for (int s0 = threadIdx.x; s0 < kLocalSlots; s0 += kB * kLocalThreads) {
+        for (int s0 = threadIdx.x; s0 < nocc; s0 += kB * kLocalThreads) {
             uint32_t kk[kB];
             int2 nbv[kB];
 #pragma unroll
             for (int u = 0; u < kB; ++u) {
-                const int slot = s0 + u * kLocalThreads;
-                kk[u] = slot < kLocalSlots ? hkey[slot] : kLocalEmpty;
+                const int i = s0 + u * kLocalThreads;
+                const int slot = i < nocc ? occ[i] : 0;
+                kk[u] = i < nocc ? hkey[slot] : kLocalEmpty;
                 nbv[u] = make_int2(-1, -1);
                 if (kk[u] != kLocalEmpty) {
                     const int64_t v = voff + (kk[u] & ((1u << kLocalVertBits) - 1));
@@ -450,8 +481,9 @@ __global__ void __launch_bounds__(kLocalThreads) k_lp_local(LocalArgs A) {
             }
 #pragma unroll
             for (int u = 0; u < kB; ++u) {
-                const int slot = s0 + u * kLocalThreads;
-                if (slot >= kLocalSlots) continue;
+                const int i = s0 + u * kLocalThreads;
+                if (i >= nocc) continue;
+                const int slot = occ[i];
                 float r = 0.f;
                 if (kk[u] != kLocalEmpty) {
                     const uint32_t nodebits = kk[u] & ~((1u << kLocalVertBits) - 1);
@@ -720,7 +752,7 @@ struct LpWork {
                     la.d1 = d1;
                     la.level = lev;
                     la.ws0 = ws0[mm];
-                    const size_t shm = (size_t)kLocalSlots * 12;
+                    const size_t shm = (size_t)kLocalSlots * 14;   // key, value, value, occupied index
                     static bool attr = false;
                     if (!attr) {
                         DCRF_TRY(cudaFuncSetAttribute(k_lp_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
