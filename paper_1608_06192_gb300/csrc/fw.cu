@@ -597,6 +597,8 @@ struct Solver {
                 DCRF_PIX_CASE(7);
                 DCRF_PIX_CASE(8);
                 DCRF_PIX_CASE(9);
+                DCRF_PIX_CASE(10);
+                DCRF_PIX_CASE(11);
             default: return pixel_v<LPc, T, POT, kPixPB[0], kPixMB[0], kPixMode[0]>(Y, phi, start, al);
             }
 #undef DCRF_PIX_CASE

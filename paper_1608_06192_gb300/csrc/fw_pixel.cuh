@@ -18,12 +18,13 @@ namespace {
 // see pixel3); kEarly gathers the corner rows while the chunk's y and lin
 // rows are still in flight to shared memory.
 constexpr int kFix = 1, kF2 = 2, kL3 = 4, kEarly = 8;
-constexpr int kPixVariants = 10;
-constexpr int kPixPB[kPixVariants] = {256, 128, 256, 128, 256, 80, 128, 256, 128, 128};
-constexpr int kPixMB[kPixVariants] = {4, 8, 3, 6, 3, 0, 6, 3, 6, 8};
+constexpr int kPixVariants = 12;
+constexpr int kPixPB[kPixVariants] = {256, 128, 256, 128, 256, 80, 128, 256, 128, 128, 128, 128};
+constexpr int kPixMB[kPixVariants] = {4, 8, 3, 6, 3, 0, 6, 3, 6, 8, 7, 8};
 constexpr int kPixMode[kPixVariants] = {0,           0,           kFix,         kFix,
                                         kFix | kF2,  kL3,         kFix | kEarly, kFix | kEarly,
-                                        kFix | kF2 | kEarly, kFix | kEarly};
+                                        kFix | kF2 | kEarly, kFix | kEarly, kFix | kF2 | kEarly,
+                                        kFix | kF2 | kEarly};
 // chunk list of a pixel-block size (256, 128 or 80 pixels)
 constexpr int chunk_list(int pb) { return pb == 256 ? 0 : (pb == 128 ? 1 : 2); }
 constexpr int chunk_warps(int list) { return list == 0 ? 8 : (list == 1 ? 4 : 8); }

@@ -1,0 +1,101 @@
+"""Edge cases at the limits of the boundary: label counts 1, 25 and 64, d = 8,
+an empty image inside a batch, and the full 32-image batch of the benchmark
+(sampled images against the oracle run alone)."""
+import numpy as np
+import pytest
+
+from helpers import gpu_setup, oracle_crf, rel_err
+from oracle import permutohedral as P
+from oracle import qp
+from paper_1608_06192_gb300 import synthetic as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("L", [1, 25, 64])
+def test_filter_label_counts(dcrf, L):
+    # L = 1 (one channel), 25 (first count above the 24-wide rows) and 64 (the maximum)
+    p = S.make_problem(40, 30, 4, max(L, 2), seed=60 + L)
+    g = gpu_setup(dcrf, [p], torch)
+    Y = np.random.default_rng(L).uniform(size=(p.n_pixels, L)).astype(np.float32)
+    for key, fkey in (("lb", "fb"), ("ls", "fs")):
+        out = dcrf.dcrf_filter(g[key], torch.from_numpy(Y).cuda()).cpu().numpy()
+        ref = P.Permutohedral(g[fkey].cpu().numpy()).filter(Y)
+        assert rel_err(out, ref) <= 1e-4
+
+
+def test_lattice_at_the_maximum_dimension(dcrf):
+    # d = 8, the largest feature dimension of the boundary
+    rng = np.random.default_rng(61)
+    f = rng.normal(scale=1.0, size=(3000, 8)).astype(np.float32)
+    lat = dcrf.dcrf_lattice_build(torch.from_numpy(f).cuda())
+    ora = P.Permutohedral(f)
+    assert lat.m == ora.m
+    Y = rng.uniform(size=(3000, 3)).astype(np.float32)
+    out = dcrf.dcrf_filter(lat, torch.from_numpy(Y).cuda()).cpu().numpy()
+    assert rel_err(out, ora.filter(Y)) <= 1e-4
+
+
+@pytest.mark.parametrize("L", [2, 64])
+def test_fw_label_counts(dcrf, L):
+    p = S.make_problem(32, 24, 4, L, seed=62 + L)
+    g = gpu_setup(dcrf, [p], torch)
+    Y = g["y0"].clone()
+    rec = dcrf.dcrf_qp_fw(g["phi"], [g["lb"], g["ls"]], p.weights, Y, 12)
+    c = oracle_crf(p)
+    y_o, _, rec_o = qp.frank_wolfe(c, p.y0, 12)
+    scale = np.abs(rec_o[:, 0]).max()
+    assert np.abs(rec[:, 0, 0] - rec_o[:, 0]).max() <= 1e-3 * scale
+    np.testing.assert_allclose(Y.cpu().numpy().sum(1), 1.0, atol=1e-5)
+
+
+def test_fw_single_label_is_fixed(dcrf):
+    # L = 1: the simplex is a point, y stays 1 and every step has gap 0
+    p = S.make_problem(20, 15, 3, 2, seed=64)
+    g = gpu_setup(dcrf, [p], torch)
+    phi = g["phi"][:, :1].contiguous()
+    Y = torch.ones((p.n_pixels, 1), device="cuda")
+    rec = dcrf.dcrf_qp_fw(phi, [g["lb"], g["ls"]], p.weights, Y, 4)
+    assert torch.all(Y == 1.0)
+    assert np.abs(rec[:, 0, 1]).max() <= 1e-6 * np.abs(rec[:, 0, 0]).max()
+
+
+def test_fw_batch_with_an_empty_image(dcrf):
+    # image 1 of three has no pixels; the others match their single-image runs
+    probs = [S.make_problem(30, 20, 4, 5, seed=65), S.make_problem(25, 18, 4, 5, seed=66)]
+    g = gpu_setup(dcrf, probs, torch)
+    n0, n1 = probs[0].n_pixels, probs[1].n_pixels
+    off = [0, n0, n0, n0 + n1]
+    lb = dcrf.dcrf_lattice_build(g["fb"], off)
+    ls = dcrf.dcrf_lattice_build(g["fs"], off)
+    Y = g["y0"].clone()
+    rec = dcrf.dcrf_qp_fw(g["phi"], [lb, ls], probs[0].weights, Y, 10)
+    assert rec.shape[1] == 3
+    assert np.all(rec[:, 1, 0] == 0.0)
+    for b, p in ((0, probs[0]), (2, probs[1])):
+        c = oracle_crf(p)
+        _, _, rec_o = qp.frank_wolfe(c, p.y0, 10)
+        scale = np.abs(rec_o[:, 0]).max()
+        assert np.abs(rec[:, b, 0] - rec_o[:, 0]).max() <= 1e-3 * scale
+
+
+def test_fw_benchmark_batch_sampled_images(dcrf):
+    # the benchmark's launch configuration (32 x 500x375, FP16 storage, the
+    # autotuned pixel kernel, graph replay on a side stream): two sampled
+    # images of the batch follow the oracle run on that image alone
+    B, iters = 32, 6
+    probs = [S.make_problem(500, 375, 30, 21, seed=i) for i in range(B)]
+    g = gpu_setup(dcrf, probs, torch)
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        Y = g["y0"].clone()
+        rec = dcrf.dcrf_qp_fw(g["phi"], [g["lb"], g["ls"]], probs[0].weights, Y, iters, storage="f16",
+                              stream=s)
+    s.synchronize()
+    for b in (0, B - 1):
+        c = oracle_crf(probs[b])
+        _, _, rec_o = qp.frank_wolfe(c, probs[b].y0, iters)
+        scale = np.abs(rec_o[:, 0]).max()
+        assert np.abs(rec[:, b, 0] - rec_o[:, 0]).max() <= 1e-3 * scale

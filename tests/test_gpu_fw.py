@@ -134,7 +134,7 @@ def test_fw_graph_path_matches_eager(dcrf):
     assert np.mean(d > 1e-4) <= 0.01
 
 
-@pytest.mark.parametrize("variant", range(10))
+@pytest.mark.parametrize("variant", range(12))
 def test_fw_every_pixel_variant(dcrf, variant, monkeypatch):
     # the autotuner chooses among these layouts of the pixel pass (block
     # shapes, index prefetch, packed FMAs, three lanes per pixel, gather
