@@ -599,6 +599,8 @@ struct Solver {
                 DCRF_PIX_CASE(9);
                 DCRF_PIX_CASE(10);
                 DCRF_PIX_CASE(11);
+                DCRF_PIX_CASE(12);
+                DCRF_PIX_CASE(13);
             default: return pixel_v<LPc, T, POT, kPixPB[0], kPixMB[0], kPixMode[0]>(Y, phi, start, al);
             }
 #undef DCRF_PIX_CASE

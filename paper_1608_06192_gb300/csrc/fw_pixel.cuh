@@ -17,14 +17,17 @@ namespace {
 // kL3 is the label-split layout (three lanes per pixel, 80 pixels per block,
 // see pixel3); kEarly gathers the corner rows while the chunk's y and lin
 // rows are still in flight to shared memory.
-constexpr int kFix = 1, kF2 = 2, kL3 = 4, kEarly = 8;
-constexpr int kPixVariants = 12;
-constexpr int kPixPB[kPixVariants] = {256, 128, 256, 128, 256, 80, 128, 256, 128, 128, 128, 128};
-constexpr int kPixMB[kPixVariants] = {4, 8, 3, 6, 3, 0, 6, 3, 6, 8, 7, 8};
+// kBulk moves the chunk's y and lin rows in and y' out with bulk (TMA) copies
+// completed on an mbarrier, where the rows are 16-byte aligned.
+constexpr int kFix = 1, kF2 = 2, kL3 = 4, kEarly = 8, kBulk = 16;
+constexpr int kPixVariants = 14;
+constexpr int kPixPB[kPixVariants] = {256, 128, 256, 128, 256, 80, 128, 256, 128, 128, 128, 128, 128, 128};
+constexpr int kPixMB[kPixVariants] = {4, 8, 3, 6, 3, 0, 6, 3, 6, 8, 7, 8, 7, 6};
 constexpr int kPixMode[kPixVariants] = {0,           0,           kFix,         kFix,
                                         kFix | kF2,  kL3,         kFix | kEarly, kFix | kEarly,
                                         kFix | kF2 | kEarly, kFix | kEarly, kFix | kF2 | kEarly,
-                                        kFix | kF2 | kEarly};
+                                        kFix | kF2 | kEarly, kFix | kF2 | kEarly | kBulk,
+                                        kFix | kF2 | kEarly | kBulk};
 // chunk list of a pixel-block size (256, 128 or 80 pixels)
 constexpr int chunk_list(int pb) { return pb == 256 ? 0 : (pb == 128 ? 1 : 2); }
 constexpr int chunk_warps(int list) { return list == 0 ? 8 : (list == 1 ? 4 : 8); }
@@ -185,6 +188,50 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// Bulk (TMA) copies between global and shared memory with an mbarrier.
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// global -> shared, completion counted on bar (16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+// Waits for phase 0 of bar with a bounded number of polls; false on timeout.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar) {
+    for (int i = 0; i < (1 << 22); ++i) {
+        unsigned done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(smem_addr(bar)) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+// shared -> global bulk store of this thread; returns after the shared source was read
+__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, unsigned bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst), "r"(smem_addr(src)),
+                 "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+// Whether the chunk's y and lin rows can move as two bulk copies: dense rows,
+// 16-byte aligned start and size on both sides.
+__device__ __forceinline__ bool tile_bulk_ok(const PixArgs &A, const Chunk &ch) {
+    const int64_t base = ch.begin * (int64_t)A.L;
+    const int64_t cnt = ch.count * (int64_t)A.L;
+    return A.y16 && A.Ls == A.L && ((base | cnt) & 3) == 0 && cnt > 0;
+}
+
 // Issues the asynchronous copies of one chunk's y and lin rows into shared
 // memory (row stride Ls); the (row, column) of element i advance incrementally.
 __device__ __forceinline__ void tile_load_async(const PixArgs &A, const Chunk &ch, float *sy, float *sl) {
@@ -289,7 +336,7 @@ __device__ __forceinline__ void gather_pair(const FwLat &la, const FwLat &lb, in
 // One chunk: every pixel of it (see the comment above PixArgs).
 template <int LP, typename TB, bool POTTS, int MODE>
 __device__ __forceinline__ void pixel_chunk(const PixArgs &A, const FwLats &F, const Chunk &ch, float *sy,
-                                            const float *sl, float (&part)[NS]) {
+                                            const float *sl, float (&part)[NS], unsigned long long *tbar) {
     const int L = A.L;
     const bool start = A.alpha == nullptr;
     const float al = start ? 0.f : (float)A.alpha[ch.image];
@@ -331,7 +378,15 @@ __device__ __forceinline__ void pixel_chunk(const PixArgs &A, const FwLats &F, c
     }
     if constexpr ((MODE & kEarly) != 0) {
         // the tile copies were left in flight during the gather
-        cp_wait<0>();
+        if (tbar) {
+            if (!mbar_wait(tbar)) {
+                // report, then wait (bounded) for the copies still in flight
+                dcrf_flag(A.status, DCRF_E_TIMEOUT);
+                mbar_wait(tbar);
+            }
+        } else {
+            cp_wait<0>();
+        }
         __syncthreads();
     }
     if (valid) {
@@ -621,16 +676,42 @@ __global__ void __launch_bounds__(PB, MB) k_fw_pixel(PixArgs A, FwLats F) {
     float *sy = smem;
     float *sl = smem + PB * A.Ls;
     const Chunk ch = A.chunks[blockIdx.x];
-    tile_load_async(A, ch, sy, sl);
-    cp_commit();
-    if constexpr ((MODE & kEarly) == 0) {
-        cp_wait<0>();
+    __shared__ __align__(8) unsigned long long tbar_s;
+    unsigned long long *tbar = nullptr;
+    if constexpr ((MODE & kBulk) != 0) {
+        static_assert((MODE & kEarly) != 0, "bulk tiles wait in the early-gather path");
+        if (tile_bulk_ok(A, ch)) tbar = &tbar_s;     // uniform over the block
+    }
+    if (tbar) {
+        if (threadIdx.x == 0) mbar_init(tbar);
         __syncthreads();
+        if (threadIdx.x == 0) {
+            const int64_t base = ch.begin * (int64_t)A.L;
+            const unsigned bytes = (unsigned)(ch.count * A.L) * 4u;
+            mbar_expect_tx(tbar, 2u * bytes);
+            bulk_g2s(sy, A.Y + base, bytes, tbar);
+            bulk_g2s(sl, A.lin + base, bytes, tbar);
+        }
+    } else {
+        tile_load_async(A, ch, sy, sl);
+        cp_commit();
+        if constexpr ((MODE & kEarly) == 0) {
+            cp_wait<0>();
+            __syncthreads();
+        }
     }
     float part[NS];
-    pixel_chunk<LP, TB, POTTS, MODE>(A, F, ch, sy, sl, part);
+    pixel_chunk<LP, TB, POTTS, MODE>(A, F, ch, sy, sl, part, tbar);
+    if (tbar) fence_proxy_async_smem();   // y' rows written here are read by the bulk store
     __syncthreads();
-    if (A.alpha != nullptr) tile_store(A, ch, sy);
+    if (A.alpha != nullptr) {
+        if (tbar) {
+            if (threadIdx.x == 0)
+                bulk_s2g(A.Y + ch.begin * (int64_t)A.L, sy, (unsigned)(ch.count * A.L) * 4u);
+        } else {
+            tile_store(A, ch, sy);
+        }
+    }
     warp_sums<NS>(part, A.cpart + (int64_t)blockIdx.x * (PB / 32) * NS);
 }
 

@@ -134,13 +134,24 @@ def test_fw_graph_path_matches_eager(dcrf):
     assert np.mean(d > 1e-4) <= 0.01
 
 
-@pytest.mark.parametrize("variant", range(12))
+@pytest.mark.parametrize("variant", range(14))
 def test_fw_every_pixel_variant(dcrf, variant, monkeypatch):
     # the autotuner chooses among these layouts of the pixel pass (block
     # shapes, index prefetch, packed FMAs, three lanes per pixel, gather
-    # during the tile copy); each must follow the oracle
+    # during the tile copy, bulk tile copies); each must follow the oracle
     monkeypatch.setenv("DCRF_PIXEL_VARIANT", str(variant))
     p = S.make_problem(96, 64, 8, 21, seed=13)
     for storage in ("f32", "f16"):
         g, Y, rec = _run_fw(dcrf, [p], 15, storage=storage)
         _check_against_oracle([p], g, Y, rec, 15, mono=1e-6 if storage == "f32" else 1e-4)
+
+
+@pytest.mark.parametrize("variant", [12, 13])
+def test_fw_bulk_variant_on_unaligned_batch(dcrf, variant, monkeypatch):
+    # chunks whose rows do not start or end on 16 bytes fall back to cp.async
+    # (image 0 ends after 851 pixels: 851 x 21 floats is not a multiple of 4)
+    monkeypatch.setenv("DCRF_PIXEL_VARIANT", str(variant))
+    probs = [S.make_problem(37, 23, 5, 21, seed=71), S.make_problem(41, 19, 5, 21, seed=72)]
+    for storage in ("f32", "f16"):
+        g, Y, rec = _run_fw(dcrf, probs, 12, storage=storage)
+        _check_against_oracle(probs, g, Y, rec, 12, mono=1e-6 if storage == "f32" else 1e-4)
