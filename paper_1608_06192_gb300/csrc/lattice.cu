@@ -163,7 +163,7 @@ __global__ void k_embed_insert(const float *__restrict__ feat, int64_t n, EmbedP
                                const int64_t *__restrict__ tab_base,
                                const int64_t *__restrict__ tab_mask,
                                unsigned long long *__restrict__ table, int64_t *__restrict__ pslot,
-                               float *__restrict__ pbary, int *__restrict__ status) {
+                               float *__restrict__ pbary, int *__restrict__ status, uint64_t max_probe) {
     constexpr int D1 = D + 1;
     int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (a >= n) return;
@@ -253,7 +253,8 @@ __global__ void k_embed_insert(const float *__restrict__ feat, int64_t n, EmbedP
             dcrf_flag(status, DCRF_E_KEY_RANGE);
         } else {
             uint64_t h = dcrf_hash64(key);
-            for (uint64_t probe = 0; probe <= mask; ++probe) {
+            const uint64_t probes = max_probe < mask ? max_probe : mask;
+            for (uint64_t probe = 0; probe <= probes; ++probe) {
                 int64_t slot = base + (int64_t)((h + probe) & mask);
                 unsigned long long cur = *((volatile unsigned long long *)&table[slot]);
                 if (cur == key) { found = slot; break; }
@@ -590,44 +591,6 @@ static dcrf_status build_typed(dcrf_lattice lat, const float *feat, cudaStream_t
     constexpr int D1 = D + 1;
     const int batch = lat->batch;
     const int64_t n = lat->n;
-    // one power-of-two table segment per image, at least twice the largest
-    // possible vertex count n_b (d+1)
-    std::vector<int64_t> base(batch), mask(batch);
-    int64_t slots = 0;
-    // testing hook: DCRF_TABLE_SLOTS caps every segment (power of two), so that
-    // the bounded probing and its DCRF_E_TABLE_FULL report can be exercised
-    int64_t cap_limit = 0;
-    if (const char *lim = std::getenv("DCRF_TABLE_SLOTS")) cap_limit = std::atoll(lim);
-    for (int b = 0; b < batch; ++b) {
-        int64_t nb = lat->point_off[b + 1] - lat->point_off[b];
-        int64_t want = 2 * nb * D1 < 64 ? 64 : 2 * nb * D1;
-        int64_t cap = 64;
-        while (cap < want) cap <<= 1;
-        if (cap_limit >= 1) {
-            int64_t c2 = 1;
-            while (c2 * 2 <= cap_limit) c2 <<= 1;
-            cap = std::min(cap, c2);
-        }
-        base[b] = slots;
-        mask[b] = cap - 1;
-        slots += cap;
-    }
-    if (slots >= (1ll << 31)) return DCRF_E_INVAL;   // vertex ids are int32
-
-    Scratch sc(s);
-    unsigned long long *table;
-    int64_t *pslot, *base_d, *mask_d;
-    int32_t *flag, *scan;
-    DCRF_CHECK_STATUS(sc.get(&table, slots));
-    DCRF_CHECK_STATUS(sc.get(&pslot, (size_t)n * D1 + 1));
-    DCRF_CHECK_STATUS(sc.get(&base_d, batch));
-    DCRF_CHECK_STATUS(sc.get(&mask_d, batch));
-    DCRF_CHECK_STATUS(sc.get(&flag, slots));
-    DCRF_CHECK_STATUS(sc.get(&scan, slots));
-    DCRF_TRY(cudaMemcpyAsync(base_d, base.data(), batch * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    DCRF_TRY(cudaMemcpyAsync(mask_d, mask.data(), batch * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    DCRF_TRY(cudaMemsetAsync(table, 0xFF, slots * sizeof(unsigned long long), s));
-
     EmbedParams P;
     const double alpha = (double)D1 * std::sqrt(2.0 / 3.0);
     for (int j = 0; j < DCRF_MAX_D; ++j)
@@ -635,11 +598,67 @@ static dcrf_status build_typed(dcrf_lattice lat, const float *feat, cudaStream_t
     P.batch = batch;
     lat->s0 = std::pow(2.0 * M_PI, D / 2.0) * std::pow(alpha, (double)D) / std::pow((double)D1, D - 0.5);
 
-    if (n > 0) {
-        ProfScope ps(P_EMBED, s);
-        k_embed_insert<D><<<blocks_for(n, 128), 128, 0, s>>>(feat, n, P, lat->point_off_d, base_d, mask_d, table,
-                                                             pslot, lat->pbary, lat->status);
-        DCRF_LAUNCHED();
+    // testing hook: DCRF_TABLE_SLOTS caps every segment (power of two), so that
+    // the bounded probing and its DCRF_E_TABLE_FULL report can be exercised
+    int64_t cap_limit = 0;
+    if (const char *lim = std::getenv("DCRF_TABLE_SLOTS")) cap_limit = std::atoll(lim);
+
+    Scratch sc(s);
+    unsigned long long *table = nullptr;
+    int64_t *pslot, *base_d, *mask_d;
+    int32_t *flag = nullptr, *scan = nullptr;
+    DCRF_CHECK_STATUS(sc.get(&pslot, (size_t)n * D1 + 1));
+    DCRF_CHECK_STATUS(sc.get(&base_d, batch));
+    DCRF_CHECK_STATUS(sc.get(&mask_d, batch));
+    int64_t slots = 0;
+    // One power-of-two table segment per image.  Vertices are far fewer than
+    // the n_b (d+1) corners (neighbouring points share them), so the first
+    // attempt sizes a segment for n_b (d+1) / 8 vertices at load <= 1/2; if a
+    // segment fills up (bounded probing reports DCRF_E_TABLE_FULL) the build
+    // runs again with room for every corner.  The table is the largest buffer
+    // of the build, so the first attempt is the cheap one.
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        std::vector<int64_t> base(batch), mask(batch);
+        slots = 0;
+        for (int b = 0; b < batch; ++b) {
+            const int64_t nb = lat->point_off[b + 1] - lat->point_off[b];
+            const int64_t corners = nb * D1;
+            int64_t want = attempt == 0 ? corners / 4 : 2 * corners;
+            if (want < 64) want = 64;
+            int64_t cap = 64;
+            while (cap < want) cap <<= 1;
+            if (cap_limit >= 1) {
+                int64_t c2 = 1;
+                while (c2 * 2 <= cap_limit) c2 <<= 1;
+                cap = std::min(cap, c2);
+            }
+            base[b] = slots;
+            mask[b] = cap - 1;
+            slots += cap;
+        }
+        if (slots >= (1ll << 31)) return DCRF_E_INVAL;   // vertex ids are int32
+        DCRF_CHECK_STATUS(sc.get(&table, slots));
+        DCRF_CHECK_STATUS(sc.get(&flag, slots));
+        DCRF_CHECK_STATUS(sc.get(&scan, slots));
+        DCRF_TRY(cudaMemcpyAsync(base_d, base.data(), batch * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        DCRF_TRY(cudaMemcpyAsync(mask_d, mask.data(), batch * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        DCRF_TRY(cudaMemsetAsync(table, 0xFF, slots * sizeof(unsigned long long), s));
+        DCRF_TRY(cudaMemsetAsync(lat->status, 0, sizeof(int), s));
+        if (n > 0) {
+            ProfScope ps(P_EMBED, s);
+            // the first attempt gives up after 256 probes (a crowded table
+            // then costs little before the second attempt)
+            k_embed_insert<D><<<blocks_for(n, 128), 128, 0, s>>>(feat, n, P, lat->point_off_d, base_d, mask_d,
+                                                                 table, pslot, lat->pbary, lat->status,
+                                                                 attempt == 0 ? 255ull : ~0ull);
+            DCRF_LAUNCHED();
+        }
+        int hstatus = 0;
+        DCRF_TRY(cudaMemcpyAsync(&hstatus, lat->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        DCRF_TRY(cudaStreamSynchronize(s));
+        if (hstatus == DCRF_E_TABLE_FULL && attempt == 0) continue;
+        if (hstatus != 0) return (dcrf_status)hstatus;
+        break;
     }
     k_occupied<<<blocks_for(slots, 256), 256, 0, s>>>(table, slots, flag);
     DCRF_LAUNCHED();
@@ -653,10 +672,7 @@ static dcrf_status build_typed(dcrf_lattice lat, const float *feat, cudaStream_t
     lat->vert_off.assign(batch + 1, 0);
     DCRF_TRY(cudaMemcpyAsync(lat->vert_off.data(), lat->vert_off_d, (batch + 1) * sizeof(int64_t),
                              cudaMemcpyDeviceToHost, s));
-    int hstatus = 0;
-    DCRF_TRY(cudaMemcpyAsync(&hstatus, lat->status, sizeof(int), cudaMemcpyDeviceToHost, s));
     DCRF_TRY(cudaStreamSynchronize(s));
-    if (hstatus != 0) return (dcrf_status)hstatus;
     lat->m = lat->vert_off[batch];
     const int64_t m = lat->m;
 
@@ -724,6 +740,7 @@ static dcrf_status build_typed(dcrf_lattice lat, const float *feat, cudaStream_t
                                                           lat->ones);
         DCRF_LAUNCHED();
     }
+    int hstatus = 0;
     DCRF_TRY(cudaMemcpyAsync(&hstatus, lat->status, sizeof(int), cudaMemcpyDeviceToHost, s));
     DCRF_TRY(cudaStreamSynchronize(s));
     if (hstatus != 0) return (dcrf_status)hstatus;
