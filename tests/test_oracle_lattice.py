@@ -150,3 +150,17 @@ def test_lattice_tracks_brute_force_on_small_image():
         lv = lat.filter(v)
         cos = np.sum(kv * lv) / np.linalg.norm(kv) / np.linalg.norm(lv)
         assert cos > min_cos
+
+
+@pytest.mark.parametrize("d", [2, 5])
+def test_lattice_operator_is_slightly_asymmetric_and_its_adjoint_is_the_transpose(d):
+    # reading c4: the per-axis blurs are symmetric but do not commute where
+    # vertices are missing, so K~ = S^T B_d ... B_0 S is not symmetric; the
+    # reverse-order blur gives exactly K~^T
+    lat = P.Permutohedral(_feats(d, 120, 20 + d, spread=2.0))
+    eye = np.eye(lat.n)
+    K = lat.filter(eye)
+    KT = lat.filter_adjoint(eye)
+    np.testing.assert_allclose(KT, K.T, rtol=0, atol=1e-12 * np.abs(K).max())
+    asym = np.linalg.norm(K - K.T) / np.linalg.norm(K)
+    assert asym > 1e-9
