@@ -149,6 +149,51 @@ __global__ void __launch_bounds__(256) k_fw_blur(BlurSet B, int p) {
     }
 }
 
+// Label-split blur pass: LP / 8 lanes per vertex row, lane q owning labels
+// 8q .. 8q+7, so that a warp instruction reads whole rows (own and both
+// neighbours) instead of one 16-byte piece of 32 rows; a warp holds
+// 32 / (LP / 8) rows (lanes beyond that are idle).  Same arithmetic as k_fw_blur.
+template <int LP, typename T>
+__global__ void __launch_bounds__(256) k_fw_blur3(BlurSet B, int p) {
+    constexpr int R = LP / 8;                  // lanes per row
+    constexpr int RW = 32 / R;                 // rows per warp
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int r = lane / R, q = lane - R * (lane / R);
+    if (r >= RW) return;
+    const int64_t g = warp * RW + r;
+    if (g >= B.start[B.nk]) return;
+    int mm = 0;
+#pragma unroll
+    for (int k = 1; k < DCRF_MAX_KERNELS; ++k)
+        if (k < B.nk && g >= B.start[k]) mm = k;
+    BlurLat lt = B.l[0];
+#pragma unroll
+    for (int k = 1; k < DCRF_MAX_KERNELS; ++k)
+        if (k == mm) lt = B.l[k];
+    if (p >= lt.d1) return;
+    const int64_t v = g - B.start[mm];
+    const int D = lt.d1 - 1;
+    T *out = ((D - p) % 2 == 0) ? (T *)lt.dst : (T *)lt.tmp;
+    const int2 nb = reinterpret_cast<const int2 *>(lt.nbr)[v * lt.d1 + p];
+    float c[8], a[8], b[8];
+    if (p == 0) {
+        row_load<float>(lt.src0, v, LP, q, c);
+        if (nb.x >= 0) row_load<float>(lt.src0, nb.x, LP, q, a);
+        if (nb.y >= 0) row_load<float>(lt.src0, nb.y, LP, q, b);
+    } else {
+        const T *in = ((D - p + 1) % 2 == 0) ? (const T *)lt.dst : (const T *)lt.tmp;
+        row_load<T>(in, v, LP, q, c);
+        if (nb.x >= 0) row_load<T>(in, nb.x, LP, q, a);
+        if (nb.y >= 0) row_load<T>(in, nb.y, LP, q, b);
+    }
+    float o[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        o[j] = 0.5f * c[j] + (nb.x >= 0 ? 0.25f * a[j] : 0.f) + (nb.y >= 0 ? 0.25f * b[j] : 0.f);
+    row_store(out, v, LP, q, o);
+}
+
 // Lattice dot products for the line search:
 //   0: w s0 sum_v sum_ij mu_ij Ylat[v][i] BS[v][j]   (= <y, K~-part of Psi s>)
 //   1: w s0 sum_v sum_ij mu_ij Slat[v][i] BS[v][j]   (= <s, K~-part of Psi s>)
@@ -371,6 +416,7 @@ struct Solver {
     Chunk *chunks_pb[3] = {nullptr, nullptr, nullptr};   // 256-, 128- and 80-pixel chunk lists
     int n_chunks_pb[3] = {0, 0, 0};
     int variant = -1;                          // chosen pixel-kernel variant
+    int blur_variant = -1;                     // chosen blur kernel (0: row per thread, 1: label-split)
     std::vector<Chunk *> vchunks;
     std::vector<int> n_vchunks;
     float *mu = nullptr, *musum = nullptr, *c = nullptr, *lin = nullptr;
@@ -685,9 +731,10 @@ struct Solver {
         return potts ? pixel_lp<float, true>(Y, phi, start) : pixel_lp<float, false>(Y, phi, start);
     }
 
-    // d+1 Jacobi passes of Slat into BS for every lattice, one launch per pass.
+    // d+1 Jacobi passes of Slat into BS for every lattice, one launch per pass
+    // (tune_only: pick the blur kernel, as run() does before graph capture).
     template <int LPc, typename T>
-    dcrf_status blur_t() {
+    dcrf_status blur_t(bool tune_only = false) {
         BlurSet B{};
         B.nk = nk;
         // lattices in order of decreasing d+1, so the ones still blurring at
@@ -707,27 +754,89 @@ struct Solver {
             B.start[k + 1] = B.start[k] + F.l[m].m;
         }
         const int dmax = nk > 0 ? B.l[0].d1 : 0;
+        if (blur_variant < 0) DCRF_CHECK_STATUS((tune_blur<LPc, T>(B, dmax)));
+        if (tune_only) return DCRF_OK;
+        return blur_passes<LPc, T>(B, dmax, blur_variant);
+    }
+
+    template <int LPc, typename T>
+    dcrf_status blur_passes(const BlurSet &B, int dmax, int variant_) {
         for (int p = 0; p < dmax; ++p) {
             int active = 0;
             while (active < nk && B.l[active].d1 > p) ++active;
             const int64_t work = B.start[active];
             if (work == 0) continue;
             ProfScope ps(P_FW_BLUR, s);
-            k_fw_blur<LPc, T><<<nblocks(work, 256), 256, 0, s>>>(B, p);
+            if (variant_ == 1) {
+                constexpr int RW = 32 / (LPc / 8);
+                const int64_t warps = (work + RW - 1) / RW;
+                k_fw_blur3<LPc, T><<<nblocks(warps * 32, 256), 256, 0, s>>>(B, p);
+            } else {
+                k_fw_blur<LPc, T><<<nblocks(work, 256), 256, 0, s>>>(B, p);
+            }
             DCRF_LAUNCHED();
         }
         return DCRF_OK;
     }
 
-    dcrf_status blur_all() {
-        if (storage == DCRF_STORAGE_F16) {
-            if (Lp == 8) return blur_t<8, __half>();
-            if (Lp == 24) return blur_t<24, __half>();
-            return blur_t<64, __half>();
+    // Blur tuner: a vertex row per thread (0) or label-split rows (1), timed on
+    // this problem's lattices (the blur only reads Slat and writes BS and tmp,
+    // which every iteration overwrites) and cached per (Lp, storage, size bucket).
+    template <int LPc, typename T>
+    dcrf_status tune_blur(const BlurSet &B, int dmax) {
+        if (const char *force = std::getenv("DCRF_BLUR_VARIANT")) {   // testing hook
+            blur_variant = std::atoi(force) == 1 ? 1 : 0;
+            return DCRF_OK;
         }
-        if (Lp == 8) return blur_t<8, float>();
-        if (Lp == 24) return blur_t<24, float>();
-        return blur_t<64, float>();
+        static std::mutex mu_;
+        static std::map<std::tuple<int, int, int>, int> cache;
+        const int64_t work = B.start[nk];
+        int bucket = 0;
+        while ((int64_t)1 << (bucket + 1) <= work) ++bucket;
+        const auto key = std::make_tuple(LPc, storage, bucket);
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            auto it = cache.find(key);
+            if (it != cache.end()) { blur_variant = it->second; return DCRF_OK; }
+        }
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        DCRF_TRY(cudaStreamIsCapturing(s, &cs));
+        if (cs != cudaStreamCaptureStatusNone || work < 4096) { blur_variant = 0; return DCRF_OK; }
+        cudaEvent_t e0, e1;
+        DCRF_TRY(cudaEventCreate(&e0));
+        DCRF_TRY(cudaEventCreate(&e1));
+        float best = 1e30f;
+        int arg = 0;
+        for (int v = 0; v < 2; ++v) {
+            DCRF_CHECK_STATUS((blur_passes<LPc, T>(B, dmax, v)));   // warm-up
+            DCRF_TRY(cudaEventRecord(e0, s));
+            for (int r = 0; r < 3; ++r) DCRF_CHECK_STATUS((blur_passes<LPc, T>(B, dmax, v)));
+            DCRF_TRY(cudaEventRecord(e1, s));
+            DCRF_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            DCRF_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            if (std::getenv("DCRF_TUNE_LOG"))
+                std::fprintf(stderr, "dcrf tune: blur Lp=%d storage=%d rows=%lld variant %d: %.1f us\n", LPc, storage,
+                             (long long)work, v, 1000.f * ms / 3.f);
+            if (ms < best) { best = ms; arg = v; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        blur_variant = arg;
+        std::lock_guard<std::mutex> lk(mu_);
+        cache[key] = arg;
+        return DCRF_OK;
+    }
+
+    dcrf_status blur_all(bool tune_only = false) {
+        if (storage == DCRF_STORAGE_F16) {
+            if (Lp == 8) return blur_t<8, __half>(tune_only);
+            if (Lp == 24) return blur_t<24, __half>(tune_only);
+            return blur_t<64, __half>(tune_only);
+        }
+        if (Lp == 8) return blur_t<8, float>(tune_only);
+        if (Lp == 24) return blur_t<24, float>(tune_only);
+        return blur_t<64, float>(tune_only);
     }
 
     template <int LPc, typename T, bool POT>
@@ -788,6 +897,7 @@ struct Solver {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         DCRF_TRY(cudaStreamIsCapturing(s, &cs));
         const bool graph_ok = s != nullptr && cs == cudaStreamCaptureStatusNone && iters >= 6 && !dcrf_profiling();
+        if (iters > 0 && blur_variant < 0) DCRF_CHECK_STATUS(blur_all(true));   // tune outside the capture
         if (graph_ok) {
             cudaGraph_t g = nullptr;
             DCRF_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));

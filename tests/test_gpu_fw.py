@@ -155,3 +155,15 @@ def test_fw_bulk_variant_on_unaligned_batch(dcrf, variant, monkeypatch):
     for storage in ("f32", "f16"):
         g, Y, rec = _run_fw(dcrf, probs, 12, storage=storage)
         _check_against_oracle(probs, g, Y, rec, 12, mono=1e-6 if storage == "f32" else 1e-4)
+
+
+@pytest.mark.parametrize("blur", [0, 1])
+@pytest.mark.parametrize("L", [5, 21, 40])
+def test_fw_each_blur_kernel(dcrf, blur, L, monkeypatch):
+    # the blur tuner chooses a row per thread (0) or label-split rows (1); both
+    # follow the oracle for 8-, 24- and 64-wide rows
+    monkeypatch.setenv("DCRF_BLUR_VARIANT", str(blur))
+    p = S.make_problem(64, 48, 6, L, seed=80 + L)
+    for storage in ("f32", "f16"):
+        g, Y, rec = _run_fw(dcrf, [p], 10, storage=storage)
+        _check_against_oracle([p], g, Y, rec, 10, mono=1e-6 if storage == "f32" else 1e-4)
