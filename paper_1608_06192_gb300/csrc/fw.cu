@@ -259,23 +259,26 @@ struct PartSums {
     int batch;
 };
 
-// Per-image sums of rows of W FP32 per-warp partials, compensated FP32
-// throughout (each thread's strided rows, warps, then across warps); each sum
-// becomes FP64 once, as hi + lo.  The result is valid in thread 0.
-template <int W>
-__device__ __forceinline__ void image_sums(const float *part, int r0, int r1, double (&out)[W]) {
-    __shared__ float rh[32][W], rl[32][W];
-    __shared__ double col[W];
-    float hi[W], lo[W];
-#pragma unroll
-    for (int q = 0; q < W; ++q) hi[q] = lo[q] = 0.f;
+// Per-image sums of per-warp FP32 partials, compensated FP32 throughout (each
+// thread's strided rows, warps, then across warps); each sum becomes FP64
+// once, as hi + lo.  rows_into adds rows [r0, r1) of width W into columns
+// OFF .. OFF+W of a thread's (hi, lo); block_sums reduces T columns over the
+// block, the result valid in thread 0.
+template <int W, int OFF, int T>
+__device__ __forceinline__ void rows_into(const float *part, int r0, int r1, float (&hi)[T], float (&lo)[T]) {
 #pragma unroll 4
     for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x)
 #pragma unroll
-        for (int q = 0; q < W; ++q) add_comp(hi[q], lo[q], part[(int64_t)r * W + q], 0.f);
+        for (int q = 0; q < W; ++q) add_comp(hi[OFF + q], lo[OFF + q], part[(int64_t)r * W + q], 0.f);
+}
+
+template <int T>
+__device__ __forceinline__ void block_sums(float (&hi)[T], float (&lo)[T], double (&out)[T]) {
+    __shared__ float rh[32][T], rl[32][T];
+    __shared__ double col[T];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int q = 0; q < W; ++q) {
+    for (int q = 0; q < T; ++q) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const float h2 = __shfl_down_sync(0xffffffffu, hi[q], o);
@@ -288,7 +291,7 @@ __device__ __forceinline__ void image_sums(const float *part, int r0, int r1, do
         }
     }
     __syncthreads();
-    if (threadIdx.x < W) {
+    if (threadIdx.x < T) {
         float h = 0.f, l = 0.f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) add_comp(h, l, rh[w][threadIdx.x], rl[w][threadIdx.x]);
         col[threadIdx.x] = (double)h + (double)l;
@@ -296,8 +299,16 @@ __device__ __forceinline__ void image_sums(const float *part, int r0, int r1, do
     __syncthreads();
     if (threadIdx.x == 0)
 #pragma unroll
-        for (int q = 0; q < W; ++q) out[q] = col[q];
-    __syncthreads();
+        for (int q = 0; q < T; ++q) out[q] = col[q];
+}
+
+template <int W>
+__device__ __forceinline__ void image_sums(const float *part, int r0, int r1, double (&out)[W]) {
+    float hi[W], lo[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) hi[q] = lo[q] = 0.f;
+    rows_into<W, 0, W>(part, r0, r1, hi, lo);
+    block_sums<W>(hi, lo, out);
 }
 
 __device__ __forceinline__ void pixel_sums(const PartSums &P, int b, double (&sg)[NS]) {
@@ -310,16 +321,22 @@ __global__ void __launch_bounds__(1024) k_fw_alpha(PartSums P, double *alpha, dc
                            int *status) {
     const int b = blockIdx.x;
     const int t = *counter;
-    double sg[NS];
-    pixel_sums(P, b, sg);
-    double yPs = sg[4], sPs = sg[5];
-    for (int m = 0; m < P.nk; ++m) {
-        double lt[2];
+    // one pass: the pixel sums in columns 0 .. NS-1, the lattice dot products
+    // of every lattice in columns NS, NS+1 (they only enter as their total)
+    constexpr int T = NS + 2;
+    float hi[T], lo[T];
+#pragma unroll
+    for (int q = 0; q < T; ++q) hi[q] = lo[q] = 0.f;
+    rows_into<NS, 0, T>(P.cpart, P.crange[b], P.crange[b + 1], hi, lo);
+#pragma unroll
+    for (int m = 0; m < DCRF_MAX_KERNELS; ++m) {
+        if (m >= P.nk) break;
         const int *vr = P.vrange + m * (P.batch + 1);
-        image_sums<2>(P.vpart, vr[b], vr[b + 1], lt);
-        yPs += lt[0];
-        sPs += lt[1];
+        rows_into<2, NS, T>(P.vpart, vr[b], vr[b + 1], hi, lo);
     }
+    double sg[T];
+    block_sums<T>(hi, lo, sg);
+    const double yPs = sg[4] + sg[NS], sPs = sg[5] + sg[NS + 1];
     if (threadIdx.x == 0) {
         const double A = sPs - sg[3] - yPs + sg[1];
         const double B = sg[2] - sg[0] + yPs - 2.0 * sg[1] + sg[3];
