@@ -26,6 +26,11 @@ import sys
 import tempfile
 import time
 
+# the oracle baseline is timed on one host thread: pin the BLAS pools before
+# numpy loads them (threadpoolctl, when present, limits them again)
+for _var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_var, "1")
+
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -91,6 +96,14 @@ def _oracle_rate(iters, seed):
     return iters / dt, dt, 1
 
 
+def workload_config(B, W, H, T, storage):
+    """The workload both arms report (the measured lattice sizes are added by ours)."""
+    return {"workload": f"{B} x {W}x{H} synthetic VOC-shaped images per GPU, L=21, "
+                        f"{storage} lattice storage, {T} Frank-Wolfe iterations per step",
+            "images_per_gpu": B, "iters_per_step": T, "storage": storage, "pixels_per_gpu": B * W * H,
+            "l2": "inputs larger than L2 (per-pixel state of the batch is several GB)"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -110,10 +123,10 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "1 x 500x375 synthetic VOC-shaped image, L=21, oracle Frank-Wolfe (FP64 numpy)",
-                   "iters_per_step": per_step},
+        "config": workload_config(args.batch, args.width, args.height, args.iters, args.storage),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{per_step} FW iterations on one 500x375 image per step"},
+                         "sample": f"each step: {per_step} oracle FW iterations (FP64 numpy) on one "
+                                   f"{args.width}x{args.height} image of the workload, scaled to image-iterations/s"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -423,12 +436,8 @@ def main():
             "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": f"{B} x {W_}x{H_} synthetic VOC-shaped images per GPU, L=21, "
-                                   f"{args.storage} lattice storage, {T} Frank-Wolfe iterations per step",
-                       "images_per_gpu": B, "iters_per_step": T, "storage": args.storage,
-                       "pixels_per_gpu": n, "vertices": {"bilateral": lb.m, "spatial": ls.m},
-                       "l2": "inputs larger than L2 (per-pixel state of the batch is several GB)",
-                       "lattice_build_s": round(build_s, 4)},
+            "config": dict(workload_config(B, W_, H_, T, args.storage),
+                           vertices={"bilateral": lb.m, "spatial": ls.m}, lattice_build_s=round(build_s, 4)),
             "plain_fp32_single_image": {"value": plain_fp32, "unit": UNIT},
             "lp_subgrad": lp,
             "dc_neg": dcneg,
