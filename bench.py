@@ -67,6 +67,26 @@ def dist_env():
     return rank, world, local
 
 
+def rank_seeds(rank: int, batch: int) -> list[int]:
+    """Seeds of the images one rank solves: disjoint across ranks (weak scaling)."""
+    return [1000 * rank + i for i in range(batch)]
+
+
+def max_over_ranks(ms: float, dist, world: int, device) -> float:
+    """The job's time is the slowest rank's (a MAX all-reduce when world > 1)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world: int, batch: int, iters: int, ms_per_step: float) -> float:
+    """Image-iterations per second of the whole job: every rank did batch x iters per step."""
+    return world * batch * iters / (ms_per_step / 1000.0)
+
+
 # ---------------------------------------------------------------------------
 # oracle (CPU) timing: the reference arm and the cpu_baseline leg
 
@@ -255,7 +275,7 @@ def main():
 
     stream = torch.cuda.Stream(device=dev)
     B, T, W_, H_ = args.batch, args.iters, args.width, args.height
-    probs = [S.make_problem(W_, H_, 30, 21, seed=1000 * rank + i) for i in range(B)]
+    probs = [S.make_problem(W_, H_, 30, 21, seed=sd) for sd in rank_seeds(rank, B)]
     L = 21
     n = sum(p.n_pixels for p in probs)
     rgb_h = torch.from_numpy(np.concatenate([p.rgb.reshape(-1, 3) for p in probs])).pin_memory()
@@ -297,13 +317,9 @@ def main():
             torch.cuda.synchronize()
         prof = D.profile_read()
         D.profile_enable(False)
-        elapsed_ms = e0.elapsed_time(e1)
-        t = torch.tensor([elapsed_ms], device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+        elapsed_ms = max_over_ranks(e0.elapsed_time(e1), dist, world, dev)
         ms_step = elapsed_ms / args.steps
-        value = world * B * T / (ms_step / 1000.0)
+        value = aggregate_rate(world, B, T, ms_step)
 
         # roofline of the dominant kernel (CUDA events on the launching stream)
         lat_m, lat_d = [lb.m, ls.m], [5, 2]
@@ -413,12 +429,8 @@ def main():
                 keep = e2e_step()
             b1.record(stream)
             stream.synchronize()
-            e2e_ms = b0.elapsed_time(b1) / k
-            tt = torch.tensor([e2e_ms], device=dev)
-            if world > 1:
-                dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_ms = float(tt.item())
-            e2e = {"value": world * B * T / (e2e_ms / 1000.0), "unit": UNIT,
+            e2e_ms = max_over_ranks(b0.elapsed_time(b1) / k, dist, world, dev)
+            e2e = {"value": aggregate_rate(world, B, T, e2e_ms), "unit": UNIT,
                    "h2d_bytes_per_step": int(rgb_h.numel() * 4 + phi_h.numel() * 4 + y0_h.numel() * 4),
                    "d2h_bytes_per_step": int(Yh.numel() * 4), "ms_per_step": round(e2e_ms, 3)}
             del keep
