@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-lp", action="store_true")
     ap.add_argument("--no-dcneg", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the CCCP and reverse-mode timings")
     return ap.parse_args()
 
 
@@ -404,6 +405,52 @@ def main():
                      "ms_per_outer_step": round(dn_ms / (outer + 1), 3),
                      "image_outer_steps_per_s": round(B * (outer + 1) / (dn_ms / 1000.0), 1)}
 
+        # CCCP on the generic DC relaxation (Section 5.1) at 320x213, L=21, FP32,
+        # 10 outer x 50 inner steps, and reverse mode through 10 unrolled
+        # Frank-Wolfe iterations on 8 images of 320x213 (forward recompute +
+        # backward), each a separate timed region
+        cccp = backward = None
+        if not args.no_extras:
+            def small_batch(k, seed0):
+                pr = [S.make_problem(320, 213, 30, 21, seed=seed0 + i) for i in range(k)]
+                nn = [q.n_pixels for q in pr]
+                of = np.concatenate([[0], np.cumsum(nn)]).astype(np.int64)
+                rg = torch.from_numpy(np.concatenate([q.rgb.reshape(-1, 3) for q in pr])).to(dev)
+                f_b, f_s = D.dcrf_features(rg, [q.width for q in pr], [q.height for q in pr], *th, stream=stream)
+                return (pr, D.dcrf_lattice_build(f_b, of, stream=stream), D.dcrf_lattice_build(f_s, of, stream=stream),
+                        torch.from_numpy(np.concatenate([q.unaries for q in pr])).to(dev),
+                        torch.from_numpy(np.concatenate([q.y0 for q in pr])).to(dev))
+
+            def timed(fn):
+                fn()
+                stream.synchronize()
+                x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                x0.record(stream)
+                fn()
+                x1.record(stream)
+                stream.synchronize()
+                return x0.elapsed_time(x1)
+
+            pc, cb, cs, cphi, cy0 = small_batch(1, 7000 + rank)
+            Yc = torch.empty_like(cy0)
+
+            def run_cccp():
+                Yc.copy_(cy0)
+                D.dcrf_qp_fw(cphi, [cb, cs], wts, Yc, 50, records=False, stream=stream)
+                D.dcrf_dc_cccp(cphi, [cb, cs], wts, Yc, 10, 50, energies=False, stream=stream)
+
+            c_ms = timed(run_cccp)
+            cccp = {"workload": "one 320x213 image, L=21, FP32: 50 QP Frank-Wolfe iterations, then CCCP "
+                                "10 outer x 50 inner", "ms": round(c_ms, 3),
+                    "fw_iterations_per_s": round(550 / (c_ms / 1000.0), 1)}
+            pg, gb, gs, gphi, gy0 = small_batch(8, 8000 + rank)
+            ybar = torch.randn(gy0.shape, generator=torch.Generator().manual_seed(1)).to(dev)
+            g_ms = timed(lambda: D.dcrf_qp_fw_backward(gphi, [gb, gs], wts, gy0, ybar, 10, stream=stream))
+            backward = {"workload": "8 x 320x213, L=21: gradient of <ybar, y^10> in the unaries and the two "
+                                    "kernel weights through 10 unrolled Frank-Wolfe iterations (forward recompute "
+                                    "included)", "ms": round(g_ms, 3),
+                        "images_per_s": round(8 / (g_ms / 1000.0), 1)}
+
         # end to end through the public API from pinned host buffers
         e2e = None
         if not args.no_e2e:
@@ -453,6 +500,8 @@ def main():
             "plain_fp32_single_image": {"value": plain_fp32, "unit": UNIT},
             "lp_subgrad": lp,
             "dc_neg": dcneg,
+            "cccp": cccp,
+            "backward": backward,
             "roofline": roof,
             "kernels": kinds,
             "cpu_baseline": cpu,
