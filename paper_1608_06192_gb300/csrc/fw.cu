@@ -664,6 +664,8 @@ struct Solver {
                 DCRF_PIX_CASE(11);
                 DCRF_PIX_CASE(12);
                 DCRF_PIX_CASE(13);
+                DCRF_PIX_CASE(14);
+                DCRF_PIX_CASE(15);
             default: return pixel_v<LPc, T, POT, kPixPB[0], kPixMB[0], kPixMode[0]>(Y, phi, start, al);
             }
 #undef DCRF_PIX_CASE

@@ -19,15 +19,18 @@ namespace {
 // rows are still in flight to shared memory.
 // kBulk moves the chunk's y and lin rows in and y' out with bulk (TMA) copies
 // completed on an mbarrier, where the rows are 16-byte aligned.
-constexpr int kFix = 1, kF2 = 2, kL3 = 4, kEarly = 8, kBulk = 16;
-constexpr int kPixVariants = 14;
-constexpr int kPixPB[kPixVariants] = {256, 128, 256, 128, 256, 80, 128, 256, 128, 128, 128, 128, 128, 128};
-constexpr int kPixMB[kPixVariants] = {4, 8, 3, 6, 3, 0, 6, 3, 6, 8, 7, 8, 7, 6};
+// kLean (Potts) computes y' and the label totals in one pass and tracks only
+// the argmin, its gradient and X(s') in the label loop.
+constexpr int kFix = 1, kF2 = 2, kL3 = 4, kEarly = 8, kBulk = 16, kLean = 32;
+constexpr int kPixVariants = 16;
+constexpr int kPixPB[kPixVariants] = {256, 128, 256, 128, 256, 80, 128, 256, 128, 128, 128, 128, 128, 128, 128, 128};
+constexpr int kPixMB[kPixVariants] = {4, 8, 3, 6, 3, 0, 6, 3, 6, 8, 7, 8, 7, 6, 7, 8};
 constexpr int kPixMode[kPixVariants] = {0,           0,           kFix,         kFix,
                                         kFix | kF2,  kL3,         kFix | kEarly, kFix | kEarly,
                                         kFix | kF2 | kEarly, kFix | kEarly, kFix | kF2 | kEarly,
                                         kFix | kF2 | kEarly, kFix | kF2 | kEarly | kBulk,
-                                        kFix | kF2 | kEarly | kBulk};
+                                        kFix | kF2 | kEarly | kBulk, kFix | kF2 | kEarly | kBulk | kLean,
+                                        kFix | kF2 | kEarly | kBulk | kLean};
 // chunk list of a pixel-block size (256, 128 or 80 pixels)
 constexpr int chunk_list(int pb) { return pb == 256 ? 0 : (pb == 128 ? 1 : 2); }
 constexpr int chunk_warps(int list) { return list == 0 ? 8 : (list == 1 ? 4 : 8); }
@@ -390,6 +393,60 @@ __device__ __forceinline__ void pixel_chunk(const PixArgs &A, const FwLats &F, c
         __syncthreads();
     }
     if (valid) {
+      if constexpr (POTTS && (MODE & kLean) != 0) {
+        // Potts, one pass for y' and the totals, then the argmin tracking only
+        // (g, s', X(s')); lin(s'), y'(s') are read back and P(s') recomputed
+        // with the same operations, so every result is the same as below
+        float *yw = sy + t * A.Ls;
+        const float ca = A.c[a];
+        float tot = 0.f, sy_ = 0.f;
+#pragma unroll
+        for (int i = 0; i < LP; ++i) {
+            if (i < L) {
+                float y = yw[i];
+                if (!start) {
+                    y = y + al * ((i == sold ? 1.f : 0.f) - y);
+                    yw[i] = y;
+                }
+                ky[i] -= A.sumw * y;          // X = K~ y' - sum_w y'
+                tot += ky[i];
+                sy_ += y;
+            }
+        }
+        const float dpot = (float)(L - 1) * ca;
+        float best = INFINITY, kys = 0.f;
+        float s0 = 0.f, s1 = 0.f, s6 = 0.f;
+#pragma unroll
+        for (int i = 0; i < LP; ++i) {
+            if (i < L) {
+                const float y = yrow[i];
+                const float P = (tot - ky[i]) + dpot * y;
+                const float li = lrow[i];
+                const float g = li + 2.f * P;
+                if (g < best) { best = g; sb = i; kys = ky[i]; }
+                s0 += li * y;
+                s1 += y * P;
+                s6 += dpot * y * y;
+            }
+        }
+        if (!(best < INFINITY)) dcrf_flag(A.status, DCRF_E_NONFINITE);
+        const float y_s = yrow[sb], lin_s = lrow[sb];
+        const float P_s = (tot - kys) + dpot * y_s;
+        part[0] = s0;
+        part[1] = s1;
+        part[2] = lin_s;
+        part[3] = P_s;
+        part[4] = -A.sumw * (sy_ - y_s) + y_s * dpot;
+        part[5] = dpot;
+        part[6] = s6;
+        if (A.phi) {
+            float sp = 0.f;
+#pragma unroll
+            for (int i = 0; i < LP; ++i)
+                if (i < L) sp += A.phi[a * L + i] * yrow[i];
+            part[7] = sp;
+        }
+      } else {
         // y' = y + alpha (e_sold - y), written over the thread's shared-memory
         // row once (it is stored back to Y after the block)
         if (!start) {
@@ -473,6 +530,7 @@ __device__ __forceinline__ void pixel_chunk(const PixArgs &A, const FwLats &F, c
                 if (i < L) sp += A.phi[a * L + i] * yp(i);
             part[7] = sp;
         }
+      }
         A.s[a] = (uint8_t)sb;
         // splat of the one-hot s' into Slat (FP32 reductions in L2).  A delta
         // update (+b at s', -b at s) does not pay: along the Frank-Wolfe path

@@ -134,7 +134,7 @@ def test_fw_graph_path_matches_eager(dcrf):
     assert np.mean(d > 1e-4) <= 0.01
 
 
-@pytest.mark.parametrize("variant", range(14))
+@pytest.mark.parametrize("variant", range(16))
 def test_fw_every_pixel_variant(dcrf, variant, monkeypatch):
     # the autotuner chooses among these layouts of the pixel pass (block
     # shapes, index prefetch, packed FMAs, three lanes per pixel, gather
@@ -146,7 +146,7 @@ def test_fw_every_pixel_variant(dcrf, variant, monkeypatch):
         _check_against_oracle([p], g, Y, rec, 15, mono=1e-6 if storage == "f32" else 1e-4)
 
 
-@pytest.mark.parametrize("variant", [12, 13])
+@pytest.mark.parametrize("variant", [12, 13, 14, 15])
 def test_fw_bulk_variant_on_unaligned_batch(dcrf, variant, monkeypatch):
     # chunks whose rows do not start or end on 16 bytes fall back to cp.async
     # (image 0 ends after 851 pixels: 851 x 21 floats is not a multiple of 4)
