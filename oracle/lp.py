@@ -119,3 +119,51 @@ def lp_solve(phi, y0, c, filter_partitioned, steps: int, beta0: float | None = N
         if e < best_e:
             best_e, best_y = e, y.copy()
     return best_y, np.array(energies)
+
+
+# ---------------------------------------------------------------------------
+# r-HST (tree) metrics, Appendix F: the LP of Eq. (rHST-LP) over the subtrees
+# T of a given tree, with y_a(T) = sum_{i in L(T)} y_a(i) and weights c_T:
+#   S(y) = phi^T y + sum_T c_T sum_{a, b != a} K_ab |y_a(T) - y_b(T)| / 2.
+# Per subtree the pixels are sorted by descending y(T) (ties by index), and
+#   dS/dy_c(k) = phi_c(k) + sum_{T containing k} c_T (sum_{a after c} K_ac
+#                                                    - sum_{a before c} K_ac),
+# the Potts model being the tree whose subtrees are the single labels with
+# c_T = 1.  `members` is the 0/1 matrix [subtrees][labels] of L(T).
+
+
+def subtree_values(y: np.ndarray, members: np.ndarray) -> np.ndarray:
+    """y_a(T) for every pixel and subtree: [N][n_subtrees]."""
+    return np.asarray(y, dtype=np.float64) @ np.asarray(members, dtype=np.float64).T
+
+
+def subgradient_tree_pairs(phi, k_dense, y, members, c_t):
+    """The Appendix F subgradient by explicit sums over each subtree's order (exact K)."""
+    Z = subtree_values(y, members)
+    G = np.array(phi, dtype=np.float64)
+    for t in range(Z.shape[1]):
+        r = label_rank(Z[:, t])
+        after = r[None, :] > r[:, None]
+        before = r[None, :] < r[:, None]
+        gt = c_t[t] * (np.sum(k_dense * after, axis=1) - np.sum(k_dense * before, axis=1))
+        G += gt[:, None] * np.asarray(members[t], dtype=np.float64)[None, :]
+    return G
+
+
+def subgradient_tree_dc(phi, y, c, filter_partitioned, members, c_t):
+    """The same with the divide and conquer of Appendix E on every subtree column."""
+    Z = subtree_values(y, members)
+    G = np.array(phi, dtype=np.float64)
+    for t in range(Z.shape[1]):
+        U = upper_sums_dc(label_rank(Z[:, t]), filter_partitioned)
+        G += (c_t[t] * (2.0 * U - c))[:, None] * np.asarray(members[t], dtype=np.float64)[None, :]
+    return G
+
+
+def s_lp_tree_pairs(phi, k_dense, y, members, c_t) -> float:
+    """The r-HST LP objective by pairs (exact K, tiny N only)."""
+    Z = subtree_values(y, members)
+    K = np.array(k_dense, dtype=np.float64)
+    np.fill_diagonal(K, 0.0)
+    pair = sum(c_t[t] * np.sum(K * np.abs(Z[:, t][:, None] - Z[:, t][None, :])) / 2.0 for t in range(Z.shape[1]))
+    return float(np.sum(phi * y) + pair)

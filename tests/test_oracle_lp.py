@@ -180,3 +180,75 @@ def test_lattice_divide_and_conquer_top_level_is_full_filter():
     lvl2 = lat.filter_partitioned(seen[2][0], seen[2][1])
     expect = np.where(rank < 4, full, 0) + np.where(seen[1][0] == 0, lvl1, 0) + np.where(seen[2][0] == 0, lvl2, 0)
     np.testing.assert_allclose(U, expect, rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# r-HST metrics (Appendix F)
+
+def _tree(L=6):
+    """A 2-level tree over 6 labels: root -> {0,1,2}, {3,4,5} -> leaves.
+
+    Subtrees below the root with the length of the edge above them (edges halve
+    downwards, an r-HST with r = 2): two groups (length 2) and six leaves (1).
+    """
+    members = np.zeros((8, L))
+    members[0, :3] = 1
+    members[1, 3:] = 1
+    for i in range(6):
+        members[2 + i, i] = 1
+    c_t = np.array([2.0, 2.0] + [1.0] * 6)
+    return members, c_t
+
+
+def _tree_distance(i, j):
+    # path length between leaves: 0, 2 (siblings: 1 + 1) or 6 (1 + 2 + 2 + 1)
+    if i == j:
+        return 0.0
+    return 2.0 if (i < 3) == (j < 3) else 6.0
+
+
+def test_potts_is_the_tree_of_single_labels():
+    n, L = 20, 4
+    k, phi, rng = _problem(11, n, L)
+    Kd = k.dense()
+    np.fill_diagonal(Kd, 0.0)
+    y = rng.dirichlet(np.ones(L), size=n)
+    c = Kd.sum(axis=1)
+    G_tree = lp.subgradient_tree_dc(phi, y, c, lp.brute_partitioned(Kd), np.eye(L), np.ones(L))
+    np.testing.assert_allclose(G_tree, lp.subgradient_dc(phi, y, c, lp.brute_partitioned(Kd)), rtol=1e-13,
+                               atol=1e-13)
+
+
+@pytest.mark.parametrize("n", [2, 9, 30])
+def test_tree_divide_and_conquer_equals_pairs(n):
+    members, c_t = _tree()
+    k, phi, rng = _problem(12 + n, n, 6)
+    Kd = k.dense()
+    np.fill_diagonal(Kd, 0.0)
+    y = rng.dirichlet(np.ones(6), size=n)
+    y[: n // 2] = y[0]                                   # ties in every subtree column
+    G_dc = lp.subgradient_tree_dc(phi, y, Kd.sum(axis=1), lp.brute_partitioned(Kd), members, c_t)
+    np.testing.assert_allclose(G_dc, lp.subgradient_tree_pairs(phi, Kd, y, members, c_t), rtol=1e-12,
+                               atol=1e-12)
+
+
+def test_tree_lp_objective_euler_identity_subgradient_and_integer_points():
+    members, c_t = _tree()
+    n = 16
+    k, phi, rng = _problem(13, n, 6)
+    Kd = k.dense()
+    np.fill_diagonal(Kd, 0.0)
+    c = Kd.sum(axis=1)
+    y = rng.dirichlet(np.ones(6), size=n)
+    G = lp.subgradient_tree_dc(phi, y, c, lp.brute_partitioned(Kd), members, c_t)
+    S = lp.s_lp_tree_pairs(phi, Kd, y, members, c_t)
+    np.testing.assert_allclose(lp.s_lp_from_g(y, G), S, rtol=1e-12)
+    for _ in range(10):                                  # convexity: G is a subgradient
+        z = rng.dirichlet(np.ones(6), size=n)
+        assert lp.s_lp_tree_pairs(phi, Kd, z, members, c_t) >= S + np.sum(G * (z - y)) - 1e-10
+    # at a labelling the LP is the tree-metric energy sum_a phi + sum_{a != b} K_ab d(x_a, x_b) / 2
+    x = rng.integers(0, 6, n)
+    Y = np.eye(6)[x]
+    E = np.sum(phi[np.arange(n), x]) + sum(Kd[a, b] * _tree_distance(x[a], x[b]) / 2.0
+                                           for a in range(n) for b in range(n) if a != b)
+    np.testing.assert_allclose(lp.s_lp_tree_pairs(phi, Kd, Y, members, c_t), E, rtol=1e-12)
