@@ -379,9 +379,24 @@ def main():
             stream.synchronize()
             lp_ms = c0.elapsed_time(c1) / reps_lp
             nlev = int(np.ceil(np.log2(n1)))
+            # the same image under a tree (r-HST) label metric (Appendix F):
+            # one sorted column per subtree of a three-level tree
+            members, c_t = S.hst_tree(L)
+            D.dcrf_lp_subgrad_tree(phi[:n1], y_lp, [l1b, l1s], wts, members, c_t, energy=False, stream=stream)
+            stream.synchronize()
+            c0.record(stream)
+            for _ in range(reps_lp):
+                D.dcrf_lp_subgrad_tree(phi[:n1], y_lp, [l1b, l1s], wts, members, c_t, energy=False, stream=stream)
+            c1.record(stream)
+            stream.synchronize()
+            tree_ms = c0.elapsed_time(c1) / reps_lp
             lp = {"workload": "one 500x375 image, L=21, y ~ Dirichlet(0.5), bilateral + spatial lattices",
                   "ms_per_subgradient": round(lp_ms, 3), "subgradients_per_s": round(1000.0 / lp_ms, 2),
-                  "label_levels_per_s": round(L * nlev * 1000.0 / lp_ms, 1)}
+                  "label_levels_per_s": round(L * nlev * 1000.0 / lp_ms, 1),
+                  "tree_metric": {"tree": "r-HST, r=2: 2 halves, groups of 4, %d leaves (%d subtrees)"
+                                          % (L, len(c_t)),
+                                  "ms_per_subgradient": round(tree_ms, 3),
+                                  "subtree_levels_per_s": round(len(c_t) * nlev * 1000.0 / tree_ms, 1)}}
 
         # CCCP for negative semi-definite compatibilities (Section 5.2) on the
         # same batch: one filter (both blur directions) and one per-pixel

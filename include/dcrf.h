@@ -273,6 +273,28 @@ dcrf_status dcrf_lp_solve(const float *unaries, const dcrf_lattice *lattices, co
                           dcrf_stream stream);
 
 /*
+ * The LP for a tree (r-HST) label metric, Appendix F: the pairwise term
+ * sum_T c_T sum_{a, b != a} K_ab |y_a(T) - y_b(T)| / 2 over the given
+ * subtrees T, with y_a(T) = sum_{i in L(T)} y_a(i).  Every subtree column is
+ * sorted (descending, ties by pixel index) and summed by the same divide and
+ * conquer, and G_a(k) = phi_a(k) + sum_{T containing k} c_T (2 U_T(a) - c_a).
+ * subtree_labels: host [n_subtrees] bit masks of L(T) (bit i = label i, L <= 64,
+ * non-empty); subtree_weights: host [n_subtrees] c_T >= 0 (the length of the
+ * edge above T).  The Potts model is the tree of single labels with c_T = 1.
+ * Otherwise as dcrf_lp_subgrad (energy = <y, G>, the tree LP objective) and
+ * dcrf_lp_solve.  DCRF_E_INVAL for an empty or out-of-range mask or a
+ * negative or non-finite weight.
+ */
+dcrf_status dcrf_lp_subgrad_tree(const float *unaries, const float *Y, const dcrf_lattice *lattices,
+                                 const float *weights, int n_kernels, int L, int n_subtrees,
+                                 const uint64_t *subtree_labels, const float *subtree_weights, float *G,
+                                 double *energy, dcrf_stream stream);
+dcrf_status dcrf_lp_solve_tree(const float *unaries, const dcrf_lattice *lattices, const float *weights,
+                               int n_kernels, int L, int n_subtrees, const uint64_t *subtree_labels,
+                               const float *subtree_weights, int steps, double beta0, float *Y,
+                               double *energies, dcrf_stream stream);
+
+/*
  * Measurement hooks (no counterpart in the paper): when enabled, every
  * kernel launch of the library is bracketed by CUDA events on its own stream
  * and solvers launch without internal graphs.  dcrf_profile_read

@@ -104,16 +104,23 @@ def default_beta0(G0: np.ndarray) -> float:
     return 0.1 / dev if dev > 0 else 0.1
 
 
-def lp_solve(phi, y0, c, filter_partitioned, steps: int, beta0: float | None = None):
-    """Algorithm 3; returns (best y, energies[steps+1] of every iterate)."""
+def lp_solve(phi, y0, c, filter_partitioned, steps: int, beta0: float | None = None, members=None, c_t=None):
+    """Algorithm 3 (Potts) or Appendix F's algorithm (tree metric, when `members`
+    and `c_t` are given); returns (best y, energies[steps+1] of every iterate)."""
     y = np.array(y0, dtype=np.float64)
-    G = subgradient_dc(phi, y, c, filter_partitioned)
+
+    def subgrad(y):
+        if members is None:
+            return subgradient_dc(phi, y, c, filter_partitioned)
+        return subgradient_tree_dc(phi, y, c, filter_partitioned, members, c_t)
+
+    G = subgrad(y)
     beta0 = default_beta0(G) if beta0 is None or beta0 <= 0 else beta0
     energies = [s_lp_from_g(y, G)]
     best_y, best_e = y.copy(), energies[0]
     for t in range(steps):
         y = project_simplex(y - (beta0 / (1.0 + t)) * G)
-        G = subgradient_dc(phi, y, c, filter_partitioned)
+        G = subgrad(y)
         e = s_lp_from_g(y, G)
         energies.append(e)
         if e < best_e:
@@ -167,3 +174,4 @@ def s_lp_tree_pairs(phi, k_dense, y, members, c_t) -> float:
     np.fill_diagonal(K, 0.0)
     pair = sum(c_t[t] * np.sum(K * np.abs(Z[:, t][:, None] - Z[:, t][None, :])) / 2.0 for t in range(Z.shape[1]))
     return float(np.sum(phi * y) + pair)
+

@@ -63,6 +63,8 @@ _SIGS = {
     "dcrf_qp_fw_backward": ([_P, _P, _P, _I, _P, _I, _I, _P, _P, _P, _P, _P, _P], _I),
     "dcrf_lp_subgrad": ([_P, _P, _P, _P, _I, _I, _P, _P, _P], _I),
     "dcrf_lp_solve": ([_P, _P, _P, _I, _I, _I, _D, _P, _P, _P], _I),
+    "dcrf_lp_subgrad_tree": ([_P, _P, _P, _P, _I, _I, _I, _P, _P, _P, _P, _P], _I),
+    "dcrf_lp_solve_tree": ([_P, _P, _P, _I, _I, _I, _P, _P, _I, _D, _P, _P, _P], _I),
     "dcrf_simplex_project": ([_P, _I64, _I, _P, _P], _I),
     "dcrf_profile_enable": ([_I], _I),
     "dcrf_profile_reset": ([], _I),
@@ -348,6 +350,52 @@ def dcrf_lp_subgrad(unaries, Y, lattices, weights, energy: bool = True, stream=N
                                  L, _ptr(G), None if e is None else e.ctypes.data_as(_P), _stream(stream)),
            "dcrf_lp_subgrad")
     return G, e
+
+
+def _tree(members, c_t, L):
+    """Subtree label sets as uint64 bit masks (from a 0/1 [subtrees][labels] matrix) and float32 weights."""
+    m = np.asarray(members)
+    if m.ndim != 2 or m.shape[1] != L:
+        raise ValueError("members must be [subtrees, L]")
+    masks = np.zeros(m.shape[0], dtype=np.uint64)
+    for t in range(m.shape[0]):
+        for i in np.nonzero(m[t])[0]:
+            masks[t] |= np.uint64(1) << np.uint64(i)
+    w = np.ascontiguousarray(np.asarray(c_t, dtype=np.float32))
+    if w.shape != (m.shape[0],):
+        raise ValueError("one weight per subtree")
+    return masks, w
+
+
+def dcrf_lp_subgrad_tree(unaries, Y, lattices, weights, members, c_t, energy: bool = True, stream=None):
+    """Tree-metric (r-HST) LP subgradient G [N, L] and objective <y, G> per image (Appendix F)."""
+    unaries = _dev(unaries, torch.float32, "unaries", 2)
+    Y = _dev(Y, torch.float32, "Y", 2)
+    L = unaries.shape[1]
+    masks, w = _tree(members, c_t, L)
+    G = torch.empty_like(Y)
+    e = np.zeros(lattices[0].batch, dtype=np.float64) if energy else None
+    _check(lib().dcrf_lp_subgrad_tree(_ptr(unaries), _ptr(Y), _handles(lattices), _floats(weights), len(lattices),
+                                      L, len(masks), masks.ctypes.data_as(_P), w.ctypes.data_as(_P), _ptr(G),
+                                      None if e is None else e.ctypes.data_as(_P), _stream(stream)),
+           "dcrf_lp_subgrad_tree")
+    return G, e
+
+
+def dcrf_lp_solve_tree(unaries, lattices, weights, Y, members, c_t, steps: int, beta0: float = 0.0,
+                       energies: bool = True, stream=None):
+    """Projected subgradient on the tree-metric LP; Y updated in place (best iterate)."""
+    unaries = _dev(unaries, torch.float32, "unaries", 2)
+    Y = _dev(Y, torch.float32, "Y", 2)
+    L = unaries.shape[1]
+    masks, w = _tree(members, c_t, L)
+    batch = lattices[0].batch
+    e = np.zeros((steps + 1) * batch, dtype=np.float64) if energies else None
+    _check(lib().dcrf_lp_solve_tree(_ptr(unaries), _handles(lattices), _floats(weights), len(lattices), L,
+                                    len(masks), masks.ctypes.data_as(_P), w.ctypes.data_as(_P), steps,
+                                    float(beta0), _ptr(Y), None if e is None else e.ctypes.data_as(_P),
+                                    _stream(stream)), "dcrf_lp_solve_tree")
+    return None if e is None else e.reshape(steps + 1, batch)
 
 
 def dcrf_lp_solve(unaries, lattices, weights, Y, steps: int, beta0: float = 0.0, energies: bool = True,

@@ -48,6 +48,23 @@ __global__ void k_lp_transpose(const float *__restrict__ Y, int64_t n, int L, fl
     vals[(int64_t)i * n + a] = (int32_t)a;
 }
 
+// Tree columns (Appendix F): keys[t][a] = y_a(T_t) = sum of y_a(i) over the
+// labels i of subtree t (bit i of mask[t]), in label order; vals[t][a] = a
+__global__ void k_lp_columns(const float *__restrict__ Y, int64_t n, int L, int C, const uint64_t *__restrict__ mask,
+                             float *__restrict__ keys, int32_t *__restrict__ vals, int *status) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n * C) return;
+    const int64_t a = q / C;
+    const int t = (int)(q - a * C);
+    const uint64_t mk = mask[t];
+    float v = 0.f;
+    for (int i = 0; i < L; ++i)
+        if ((mk >> i) & 1ull) v += Y[a * L + i];
+    if (!isfinite(v)) dcrf_flag(status, DCRF_E_NONFINITE);
+    keys[(int64_t)t * n + a] = v + 0.0f;
+    vals[(int64_t)t * n + a] = (int32_t)a;
+}
+
 // seg offsets for (label, image): begin = i*n + off[b]
 __global__ void k_lp_segments(const int64_t *__restrict__ off, int batch, int L, int64_t n,
                               int64_t *__restrict__ begin, int64_t *__restrict__ end) {
@@ -244,6 +261,47 @@ __global__ void k_lp_combine(const float *__restrict__ phi, const float *__restr
     }
     if (energy) {
         // one atomic per warp when the warp lies in one image
+        const int lane = threadIdx.x & 31;
+        const int img0 = __shfl_sync(0xffffffffu, img, 0);
+        const bool uni = __all_sync(0xffffffffu, img == img0 || img < 0);
+        if (uni) {
+            double sum = part;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+            if (lane == 0 && img0 >= 0) atomicAdd(energy + img0, sum);
+        } else if (img >= 0) {
+            atomicAdd(energy + img, part);
+        }
+    }
+}
+
+// Tree combine (Appendix F): G_a(k) = phi_a(k) + sum over subtrees t containing
+// k of w_t (2 U_t(a) - c_a); energy[b] += <y, G> over image b
+__global__ void k_lp_combine_tree(const float *__restrict__ phi, const float *__restrict__ Y,
+                                  const float *__restrict__ U, const int32_t *__restrict__ inv,
+                                  const float *__restrict__ c, int64_t n, int L, int C,
+                                  const uint64_t *__restrict__ mask, const float *__restrict__ wt,
+                                  const int64_t *__restrict__ off, int batch, float *__restrict__ G,
+                                  double *__restrict__ energy) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double part = 0.0;
+    int img = -1;
+    if (q < n * L) {
+        const int64_t a = q / L;
+        const int k = (int)(q - a * L);
+        float g = phi[q];
+        for (int t = 0; t < C; ++t)
+            if ((mask[t] >> k) & 1ull) g += wt[t] * (2.f * U[(int64_t)t * n + inv[(int64_t)t * n + a]] - c[a]);
+        G[q] = g;
+        part = (double)Y[q] * g;
+        int lo = 0, hi = batch - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= a) lo = mid; else hi = mid - 1;
+        }
+        img = lo;
+    }
+    if (energy) {
         const int lane = threadIdx.x & 31;
         const int img0 = __shfl_sync(0xffffffffu, img, 0);
         const bool uni = __all_sync(0xffffffffu, img == img0 || img < 0);
@@ -528,6 +586,9 @@ struct LpWork {
     Scratch sc;
     const dcrf_lattice *lats = nullptr;
     int nk = 0, L = 0, batch = 0;
+    int C = 0;                        // sorted columns: the labels (Potts) or the subtrees (tree metric)
+    uint64_t *cmask = nullptr;        // [C] label sets of the subtrees (tree metric only)
+    float *cw = nullptr;              // [C] subtree weights c_T
     int64_t n = 0;
     float sumw = 0.f;
     float ws0[DCRF_MAX_KERNELS];
@@ -554,12 +615,28 @@ struct LpWork {
 
     explicit LpWork(cudaStream_t st) : s(st), sc(st) {}
 
-    dcrf_status setup(const dcrf_lattice *lattices, const float *weights, int n_k, int L_) {
+    // Potts: masks == nullptr (one column per label); tree metric: n_sub
+    // subtrees with label masks and weights (host arrays).
+    dcrf_status setup(const dcrf_lattice *lattices, const float *weights, int n_k, int L_, int n_sub = 0,
+                      const uint64_t *masks = nullptr, const float *c_sub = nullptr) {
         DCRF_CHECK_STATUS(dcrf_check_lattices(lattices, n_k));
         if (!weights || L_ < 1 || L_ > DCRF_MAX_L) return DCRF_E_INVAL;
         lats = lattices;
         nk = n_k;
         L = L_;
+        C = L;
+        if (masks) {
+            if (!c_sub || n_sub < 1) return DCRF_E_INVAL;
+            const uint64_t all = L_ == 64 ? ~0ull : ((1ull << L_) - 1);
+            for (int t = 0; t < n_sub; ++t)
+                if (masks[t] == 0 || (masks[t] & ~all) || !(c_sub[t] >= 0.f) || !std::isfinite(c_sub[t]))
+                    return DCRF_E_INVAL;
+            C = n_sub;
+            DCRF_CHECK_STATUS(sc.get(&cmask, (size_t)C));
+            DCRF_CHECK_STATUS(sc.get(&cw, (size_t)C));
+            DCRF_TRY(cudaMemcpyAsync(cmask, masks, C * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+            DCRF_TRY(cudaMemcpyAsync(cw, c_sub, C * sizeof(float), cudaMemcpyHostToDevice, s));
+        }
         n = lattices[0]->n;
         batch = lattices[0]->batch;
         sumw = 0.f;
@@ -567,7 +644,7 @@ struct LpWork {
             if (!(weights[m] >= 0.f)) return DCRF_E_INVAL;
             sumw += weights[m];
             ws0[m] = (float)(weights[m] * lattices[m]->s0);
-            Emax = std::max<int64_t>(Emax, n * L * (lattices[m]->d + 1));
+            Emax = std::max<int64_t>(Emax, n * C * (lattices[m]->d + 1));
         }
         if (Emax >= (1ll << 31)) return DCRF_E_INVAL;
         std::vector<int32_t> nlev(batch);
@@ -577,8 +654,8 @@ struct LpWork {
         }
         DCRF_CHECK_STATUS(sc.get(&off_d, batch + 1));
         DCRF_CHECK_STATUS(sc.get(&nlev_d, batch));
-        DCRF_CHECK_STATUS(sc.get(&seg_b, (size_t)L * batch));
-        DCRF_CHECK_STATUS(sc.get(&seg_e, (size_t)L * batch));
+        DCRF_CHECK_STATUS(sc.get(&seg_b, (size_t)C * batch));
+        DCRF_CHECK_STATUS(sc.get(&seg_e, (size_t)C * batch));
         DCRF_TRY(cudaMemcpyAsync(off_d, lattices[0]->point_off.data(), (batch + 1) * sizeof(int64_t),
                                  cudaMemcpyHostToDevice, s));
         DCRF_TRY(cudaMemcpyAsync(nlev_d, nlev.data(), batch * sizeof(int32_t), cudaMemcpyHostToDevice, s));
@@ -600,13 +677,13 @@ struct LpWork {
         }
         for (int b = 0; b < batch; ++b) {
             const int64_t nb_ = lattices[0]->point_off[b + 1] - lattices[0]->point_off[b];
-            max_blocks += (size_t)L * (size_t)((nb_ + kLocalP - 1) / kLocalP);
+            max_blocks += (size_t)C * (size_t)((nb_ + kLocalP - 1) / kLocalP);
         }
         DCRF_CHECK_STATUS(sc.get(&lblocks, max_blocks));
         lblocks_cap = max_blocks;
-        k_lp_segments<<<nb(L * batch, 128), 128, 0, s>>>(off_d, batch, L, n, seg_b, seg_e);
+        k_lp_segments<<<nb(C * batch, 128), 128, 0, s>>>(off_d, batch, C, n, seg_b, seg_e);
         DCRF_LAUNCHED();
-        const size_t nl = (size_t)(n > 0 ? n : 1) * L;
+        const size_t nl = (size_t)(n > 0 ? n : 1) * C;   // sorted columns
         DCRF_CHECK_STATUS(sc.get(&c, (size_t)(n > 0 ? n : 1)));
         DCRF_CHECK_STATUS(sc.get(&keys, nl));
         DCRF_CHECK_STATUS(sc.get(&keys2, nl));
@@ -634,7 +711,7 @@ struct LpWork {
         // temp storage for the sorts and scans
         size_t t1 = 0, t2 = 0, t3 = 0;
         DCRF_TRY(cub::DeviceSegmentedRadixSort::SortPairsDescending(nullptr, t1, keys, keys2, vals, perm, (int)nl,
-                                                                     L * batch, seg_b, seg_e, 0, 32, s));
+                                                                     C * batch, seg_b, seg_e, 0, 32, s));
         DCRF_TRY(cub::DeviceRadixSort::SortPairs(nullptr, t2, ekey, ekey2, eq, eq2, (int)ne, 0, 64, s));
         DCRF_TRY(cub::DeviceScan::InclusiveSum(nullptr, t3, flag, rid, (int)ne, s));
         tmp_bytes = std::max(t1, std::max(t2, t3));
@@ -677,17 +754,18 @@ struct LpWork {
     // G = phi + 2U - c; energy[b] += <y, G> over image b (energy zeroed by caller)
     dcrf_status subgrad(const float *phi, const float *Y, float *G, double *energy) {
         if (n == 0) return DCRF_OK;
-        const int64_t nl = n * L;
-        const int status_lat = 0;
-        (void)status_lat;
+        const int64_t nl = n * C;        // sorted columns x pixels
         {
             ProfScope ps(P_LP_SORT, s);
-            k_lp_transpose<<<nb(nl, 256), 256, 0, s>>>(Y, n, L, keys, vals, lats[0]->status);
+            if (cmask)
+                k_lp_columns<<<nb(nl, 256), 256, 0, s>>>(Y, n, L, C, cmask, keys, vals, lats[0]->status);
+            else
+                k_lp_transpose<<<nb(nl, 256), 256, 0, s>>>(Y, n, L, keys, vals, lats[0]->status);
             DCRF_LAUNCHED();
             size_t tb = tmp_bytes;
             DCRF_TRY(cub::DeviceSegmentedRadixSort::SortPairsDescending(tmp, tb, keys, keys2, vals, perm, (int)nl,
-                                                                         L * batch, seg_b, seg_e, 0, 32, s));
-            k_lp_inverse<<<nb(nl, 256), 256, 0, s>>>(perm, n, L, inv);
+                                                                         C * batch, seg_b, seg_e, 0, 32, s));
+            k_lp_inverse<<<nb(nl, 256), 256, 0, s>>>(perm, n, C, inv);
             DCRF_LAUNCHED();
         }
         DCRF_TRY(cudaMemsetAsync(U, 0, nl * sizeof(float), s));
@@ -697,10 +775,10 @@ struct LpWork {
             const int64_t E = nl * d1;
             const int64_t m = lat->m > 0 ? lat->m : 1;
             int keybits = 1;
-            while (keybits < 64 && ((uint64_t)L * (uint64_t)m) > (1ull << keybits)) ++keybits;
+            while (keybits < 64 && ((uint64_t)C * (uint64_t)m) > (1ull << keybits)) ++keybits;
             {
                 ProfScope ps(P_LP_SORT, s);
-                k_lp_entries<<<nb(E, 256), 256, 0, s>>>(perm, n, L, d1, lat->pvid, m, ekey, eq);
+                k_lp_entries<<<nb(E, 256), 256, 0, s>>>(perm, n, C, d1, lat->pvid, m, ekey, eq);
                 DCRF_LAUNCHED();
                 size_t tb = tmp_bytes;
                 DCRF_TRY(cub::DeviceRadixSort::SortPairs(tmp, tb, ekey, ekey2, eq, eq2, (int)E, 0, keybits, s));
@@ -730,7 +808,7 @@ struct LpWork {
                     if (lev >= nlev_h[b]) continue;
                     if (lev >= local_from_h[mm][b]) {
                         const int64_t nb_ = lat->point_off[b + 1] - lat->point_off[b];
-                        for (int i = 0; i < L; ++i)
+                        for (int i = 0; i < C; ++i)
                             for (int64_t p0 = 0; p0 < nb_; p0 += kLocalP) lb.push_back(LocalBlock{i, b, (int32_t)p0});
                     } else {
                         any_global = true;
@@ -804,7 +882,11 @@ struct LpWork {
         }
         {
             ProfScope ps(P_LP_COMBINE, s);
-            k_lp_combine<<<nb(nl, 256), 256, 0, s>>>(phi, Y, U, inv, c, n, L, off_d, batch, G, energy);
+            if (cmask)
+                k_lp_combine_tree<<<nb(n * L, 256), 256, 0, s>>>(phi, Y, U, inv, c, n, L, C, cmask, cw, off_d,
+                                                                  batch, G, energy);
+            else
+                k_lp_combine<<<nb(nl, 256), 256, 0, s>>>(phi, Y, U, inv, c, n, L, off_d, batch, G, energy);
             DCRF_LAUNCHED();
         }
         return DCRF_OK;
@@ -864,13 +946,14 @@ __global__ void k_lp_copy_rows(const float *__restrict__ src, float *__restrict_
 
 }  // namespace
 
-extern "C" dcrf_status dcrf_lp_subgrad(const float *unaries, const float *Y, const dcrf_lattice *lattices,
-                                       const float *weights, int n_kernels, int L, float *G, double *energy,
-                                       dcrf_stream stream) {
+namespace {
+
+dcrf_status lp_subgrad_impl(const float *unaries, const float *Y, const dcrf_lattice *lattices, const float *weights,
+                            int n_kernels, int L, int n_sub, const uint64_t *masks, const float *c_sub, float *G,
+                            double *energy, cudaStream_t s) {
     if (!unaries || !Y || !G) return DCRF_E_INVAL;
-    cudaStream_t s = (cudaStream_t)stream;
     LpWork W(s);
-    DCRF_CHECK_STATUS(W.setup(lattices, weights, n_kernels, L));
+    DCRF_CHECK_STATUS(W.setup(lattices, weights, n_kernels, L, n_sub, masks, c_sub));
     double *e;
     DCRF_CHECK_STATUS(W.sc.get(&e, (size_t)W.batch));
     DCRF_TRY(cudaMemsetAsync(e, 0, W.batch * sizeof(double), s));
@@ -885,13 +968,12 @@ extern "C" dcrf_status dcrf_lp_subgrad(const float *unaries, const float *Y, con
     return DCRF_OK;
 }
 
-extern "C" dcrf_status dcrf_lp_solve(const float *unaries, const dcrf_lattice *lattices, const float *weights,
-                                     int n_kernels, int L, int steps, double beta0, float *Y, double *energies,
-                                     dcrf_stream stream) {
+dcrf_status lp_solve_impl(const float *unaries, const dcrf_lattice *lattices, const float *weights, int n_kernels,
+                          int L, int n_sub, const uint64_t *masks, const float *c_sub, int steps, double beta0,
+                          float *Y, double *energies, cudaStream_t s) {
     if (!unaries || !Y || steps < 0) return DCRF_E_INVAL;
-    cudaStream_t s = (cudaStream_t)stream;
     LpWork W(s);
-    DCRF_CHECK_STATUS(W.setup(lattices, weights, n_kernels, L));
+    DCRF_CHECK_STATUS(W.setup(lattices, weights, n_kernels, L, n_sub, masks, c_sub));
     if (W.n == 0) return DCRF_OK;
     const int batch = W.batch;
     const int64_t nl = W.n * L;
@@ -937,6 +1019,40 @@ extern "C" dcrf_status dcrf_lp_solve(const float *unaries, const dcrf_lattice *l
         if (h != 0) return (dcrf_status)h;
     }
     return DCRF_OK;
+}
+
+}  // namespace
+
+extern "C" dcrf_status dcrf_lp_subgrad(const float *unaries, const float *Y, const dcrf_lattice *lattices,
+                                       const float *weights, int n_kernels, int L, float *G, double *energy,
+                                       dcrf_stream stream) {
+    return lp_subgrad_impl(unaries, Y, lattices, weights, n_kernels, L, 0, nullptr, nullptr, G, energy,
+                           (cudaStream_t)stream);
+}
+
+extern "C" dcrf_status dcrf_lp_subgrad_tree(const float *unaries, const float *Y, const dcrf_lattice *lattices,
+                                            const float *weights, int n_kernels, int L, int n_subtrees,
+                                            const uint64_t *subtree_labels, const float *subtree_weights, float *G,
+                                            double *energy, dcrf_stream stream) {
+    if (!subtree_labels || !subtree_weights) return DCRF_E_INVAL;
+    return lp_subgrad_impl(unaries, Y, lattices, weights, n_kernels, L, n_subtrees, subtree_labels,
+                           subtree_weights, G, energy, (cudaStream_t)stream);
+}
+
+extern "C" dcrf_status dcrf_lp_solve(const float *unaries, const dcrf_lattice *lattices, const float *weights,
+                                     int n_kernels, int L, int steps, double beta0, float *Y, double *energies,
+                                     dcrf_stream stream) {
+    return lp_solve_impl(unaries, lattices, weights, n_kernels, L, 0, nullptr, nullptr, steps, beta0, Y, energies,
+                         (cudaStream_t)stream);
+}
+
+extern "C" dcrf_status dcrf_lp_solve_tree(const float *unaries, const dcrf_lattice *lattices, const float *weights,
+                                          int n_kernels, int L, int n_subtrees, const uint64_t *subtree_labels,
+                                          const float *subtree_weights, int steps, double beta0, float *Y,
+                                          double *energies, dcrf_stream stream) {
+    if (!subtree_labels || !subtree_weights) return DCRF_E_INVAL;
+    return lp_solve_impl(unaries, lattices, weights, n_kernels, L, n_subtrees, subtree_labels, subtree_weights, steps,
+                         beta0, Y, energies, (cudaStream_t)stream);
 }
 
 extern "C" dcrf_status dcrf_simplex_project(const float *V, int64_t n, int L, float *Y, dcrf_stream stream) {

@@ -117,6 +117,31 @@ def crop(p: Problem, width: int, height: int, x0: int = 0, y0: int = 0) -> Probl
                    p.y0[idx].copy(), p.seed, p.weights, p.thetas)
 
 
+def hst_tree(n_labels: int, group: int = 4):
+    """A synthetic three-level r-HST (r = 2) over the labels, given as the
+    subtrees below the root: two halves (edge length 4), groups of up to
+    `group` consecutive labels inside each half (length 2, groups of one
+    label omitted) and the single labels (length 1).  Returns the 0/1 matrix
+    [subtrees][labels] of the label sets and the edge lengths."""
+    halves = [list(range(0, n_labels // 2)), list(range(n_labels // 2, n_labels))]
+    rows, lengths = [], []
+
+    def add(labels, length):
+        m = np.zeros(n_labels)
+        m[labels] = 1.0
+        rows.append(m)
+        lengths.append(length)
+
+    for h in halves:
+        if len(h) > 1:
+            add(h, 4.0)
+        for s in range(0, len(h), group):
+            if len(h[s:s + group]) > 1:
+                add(h[s:s + group], 2.0)
+    for i in range(n_labels):
+        add([i], 1.0)
+    return np.array(rows), np.array(lengths)
+
 # The five workloads, by what they are.
 def qp_small():        # 64x48, 5 regions, L=5, seed 0
     return make_problem(64, 48, 5, 5, 0)
