@@ -20,6 +20,15 @@ Section 6 of the paper, Potts model, FP64:
   beta0 = 0.1 / max |G0_a(i) - mean_i G0_a(i)| by default (reading c14); the
   projection onto the simplex (Condat's problem) is computed here by the
   sort-based closed form, which gives the same unique point.
+* Section 5 (end): the LP point is turned into a labelling by the randomised
+  rounding of Kleinberg and Tardos (uniform metric): repeatedly draw a label i
+  uniformly and a threshold alpha uniformly in [0, 1), and give label i to
+  every still unlabelled pixel a with y_a(i) > alpha.  The draws are inputs
+  here (phase_labels, phase_thresholds); the comparison is taken in FP32, the
+  precision y is stored in (reading: the decision of an integer in the
+  kernel's precision).  Pixel a gets label i with probability y_a(i), and two
+  pixels are separated with probability at most 2d/(1+d), d = |y_a - y_b|_1 / 2,
+  which is at most twice their LP distance: the factor 2 for the Potts model.
 """
 from __future__ import annotations
 
@@ -175,3 +184,38 @@ def s_lp_tree_pairs(phi, k_dense, y, members, c_t) -> float:
     pair = sum(c_t[t] * np.sum(K * np.abs(Z[:, t][:, None] - Z[:, t][None, :])) / 2.0 for t in range(Z.shape[1]))
     return float(np.sum(phi * y) + pair)
 
+
+# ---------------------------------------------------------------------------
+# Kleinberg-Tardos rounding of an LP point (uniform metric).
+
+
+def kt_round(y: np.ndarray, phase_labels, phase_thresholds, labels=None) -> np.ndarray:
+    """Labels after the given phases; -1 marks a pixel no phase has labelled.
+
+    Phase t gives label phase_labels[t] to every unlabelled pixel a with
+    y_a(phase_labels[t]) > phase_thresholds[t] (both in FP32).  `labels`
+    (optional) is a previous result to continue from: its entries >= 0 stay.
+    """
+    y32 = np.asarray(y, dtype=np.float32)
+    out = np.full(y32.shape[0], -1, dtype=np.int32) if labels is None else np.array(labels, dtype=np.int32)
+    for i, alpha in zip(np.asarray(phase_labels), np.asarray(phase_thresholds, dtype=np.float32)):
+        hit = (out < 0) & (y32[:, int(i)] > alpha)
+        out[hit] = int(i)
+    return out
+
+
+def kt_separation_probability(ya: np.ndarray, yb: np.ndarray) -> float:
+    """Exact probability that the rounding gives two pixels different labels.
+
+    Until one of them is labelled, a phase labels both (label i, threshold
+    below min(ya(i), yb(i))) or exactly one of them; the first such event
+    decides.  Both together: the same label.  One alone with label i: the
+    other later draws its label from its own marginal, equal to i with
+    probability y(i).  The events of one phase have weights min_i, (ya-yb)+_i
+    and (yb-ya)+_i, summing to 1 + d with d = |ya - yb|_1 / 2.
+    """
+    a = np.asarray(ya, np.float64)
+    b = np.asarray(yb, np.float64)
+    d = 0.5 * float(np.abs(a - b).sum())
+    same = float(np.sum(np.minimum(a, b) + np.maximum(a - b, 0.0) * b + np.maximum(b - a, 0.0) * a))
+    return 1.0 - same / (1.0 + d)

@@ -92,6 +92,14 @@ def dirichlet_labels(n: int, n_labels: int, seed: int, concentration: float = 0.
     return y.astype(np.float32)
 
 
+def kt_phases(n_labels: int, count: int, seed: int):
+    """Random draws of the Kleinberg-Tardos rounding: `count` labels uniform
+    in [0, n_labels) (int32) and thresholds uniform in [0, 1) (float32)."""
+    rng = np.random.default_rng(seed)
+    return (rng.integers(0, n_labels, size=count).astype(np.int32),
+            rng.random(count, dtype=np.float32))
+
+
 def batch_sizes(count: int, seed: int, w_range=(240, 500), h_range=(160, 500)):
     """Image sizes W ~ U[240,500], H ~ U[160,500] (integers, inclusive)."""
     rng = np.random.default_rng(seed)
