@@ -390,13 +390,25 @@ def main():
             c1.record(stream)
             stream.synchronize()
             tree_ms = c0.elapsed_time(c1) / reps_lp
+            # Kleinberg-Tardos rounding of that point (700 phases label every
+            # pixel but with probability ~1e-10)
+            pl, pt = S.kt_phases(L, 700, seed=6)
+            D.dcrf_round_kt(y_lp, pl, pt, count=False, stream=stream)
+            stream.synchronize()
+            c0.record(stream)
+            for _ in range(reps_lp):
+                D.dcrf_round_kt(y_lp, pl, pt, count=False, stream=stream)
+            c1.record(stream)
+            stream.synchronize()
+            kt_ms = c0.elapsed_time(c1) / reps_lp
             lp = {"workload": "one 500x375 image, L=21, y ~ Dirichlet(0.5), bilateral + spatial lattices",
                   "ms_per_subgradient": round(lp_ms, 3), "subgradients_per_s": round(1000.0 / lp_ms, 2),
                   "label_levels_per_s": round(L * nlev * 1000.0 / lp_ms, 1),
                   "tree_metric": {"tree": "r-HST, r=2: 2 halves, groups of 4, %d leaves (%d subtrees)"
                                           % (L, len(c_t)),
                                   "ms_per_subgradient": round(tree_ms, 3),
-                                  "subtree_levels_per_s": round(len(c_t) * nlev * 1000.0 / tree_ms, 1)}}
+                                  "subtree_levels_per_s": round(len(c_t) * nlev * 1000.0 / tree_ms, 1)},
+                  "kt_rounding": {"phases": 700, "ms": round(kt_ms, 4)}}
 
         # CCCP for negative semi-definite compatibilities (Section 5.2) on the
         # same batch: one filter (both blur directions) and one per-pixel

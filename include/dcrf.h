@@ -238,6 +238,25 @@ dcrf_status dcrf_mean_field(const float *unaries, const dcrf_lattice *lattices, 
 dcrf_status dcrf_round(const float *Y, int64_t n, int L, int32_t *labels, float *onehot, dcrf_stream stream);
 
 /*
+ * Kleinberg-Tardos rounding of an LP point (end of Section 5: the rounding
+ * that gives the LP its factor 2 for the Potts model).  Phase t gives label
+ * phase_labels[t] to every unlabelled pixel a with
+ * Y[a][phase_labels[t]] > phase_thresholds[t] (FP32 comparison).  The random
+ * draws are inputs: host arrays [n_phases] with labels uniform in [0, L) and
+ * thresholds uniform in [0, 1), copied before the call returns.  Y: device
+ * FP32 [N][L] (rows on the simplex); labels: device int32 [N], written with
+ * the first label each pixel gets, -1 where no phase labelled it; with
+ * resume != 0 its entries >= 0 are kept as they are and only the others are
+ * processed (a run continued with further phases).  With T phases a pixel
+ * stays unlabelled with probability (1 - 1/L)^T.  unassigned: host, the
+ * number of pixels left at -1 (synchronises), or NULL (asynchronous).
+ * DCRF_E_INVAL for a phase label outside [0, L) or a threshold outside [0, 1).
+ */
+dcrf_status dcrf_round_kt(const float *Y, int64_t n, int L, int n_phases, const int32_t *phase_labels,
+                          const float *phase_thresholds, int resume, int32_t *labels, int64_t *unassigned,
+                          dcrf_stream stream);
+
+/*
  * Energy of a labelling, Eq. 1 (ordered pairs, pixel operator through the
  * lattices): E(x) = S_QP at the one-hot rows of x.  labels: device int32 [N]
  * in [0, L) (else DCRF_E_INVAL); energy: host [batch] (synchronises).

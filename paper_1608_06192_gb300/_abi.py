@@ -65,6 +65,7 @@ _SIGS = {
     "dcrf_lp_solve": ([_P, _P, _P, _I, _I, _I, _D, _P, _P, _P], _I),
     "dcrf_lp_subgrad_tree": ([_P, _P, _P, _P, _I, _I, _I, _P, _P, _P, _P, _P], _I),
     "dcrf_lp_solve_tree": ([_P, _P, _P, _I, _I, _I, _P, _P, _I, _D, _P, _P, _P], _I),
+    "dcrf_round_kt": ([_P, _I64, _I, _I, _P, _P, _I, _P, _P, _P], _I),
     "dcrf_simplex_project": ([_P, _I64, _I, _P, _P], _I),
     "dcrf_profile_enable": ([_I], _I),
     "dcrf_profile_reset": ([], _I),
@@ -323,6 +324,28 @@ def dcrf_round(Y, onehot: bool = False, stream=None):
     _check(lib().dcrf_round(_ptr(Y), Y.shape[0], Y.shape[1], _ptr(labels), None if oh is None else _ptr(oh),
                             _stream(stream)), "dcrf_round")
     return (labels, oh) if onehot else labels
+
+
+def dcrf_round_kt(Y, phase_labels, phase_thresholds, labels=None, count: bool = True, stream=None):
+    """Kleinberg-Tardos rounding with the given phases (host int32 labels, float32
+    thresholds in [0, 1)).  Continues from `labels` when given (entries >= 0
+    kept, updated in place).  Returns (labels int32 [N], pixels left at -1 or None)."""
+    Y = _dev(Y, torch.float32, "Y", 2)
+    pl = np.ascontiguousarray(np.asarray(phase_labels, dtype=np.int32))
+    pt = np.ascontiguousarray(np.asarray(phase_thresholds, dtype=np.float32))
+    if pl.shape != pt.shape or pl.ndim != 1:
+        raise ValueError("one threshold per phase label")
+    resume = labels is not None
+    if resume:
+        labels = _dev(labels, torch.int32, "labels", 1)
+    else:
+        labels = torch.empty(Y.shape[0], dtype=torch.int32, device=Y.device)
+    left = np.zeros(1, dtype=np.int64) if count else None
+    _check(lib().dcrf_round_kt(_ptr(Y), Y.shape[0], Y.shape[1], len(pl), pl.ctypes.data_as(_P),
+                               pt.ctypes.data_as(_P), int(resume), _ptr(labels),
+                               None if left is None else left.ctypes.data_as(_P), _stream(stream)),
+           "dcrf_round_kt")
+    return labels, (None if left is None else int(left[0]))
 
 
 def dcrf_labelling_energy(unaries, lattices, weights, labels, compat=None, storage="f32", stream=None):

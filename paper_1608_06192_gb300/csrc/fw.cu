@@ -1420,6 +1420,35 @@ __global__ void k_round(const float *__restrict__ Y, int64_t n, int L, int32_t *
         for (int i = 0; i < L; ++i) onehot[a * L + i] = i == arg ? 1.f : 0.f;
 }
 
+// Kleinberg-Tardos rounding (end of Section 5): phase t gives label plab[t]
+// to every unlabelled pixel whose y of that label exceeds pthr[t].  One thread
+// per pixel walks the phases until its first hit; the phase arrays are read by
+// every thread of a warp at once (broadcast loads).
+__global__ void k_round_kt(const float *__restrict__ Y, int64_t n, int L, const int32_t *__restrict__ plab,
+                           const float *__restrict__ pthr, int T, int resume, int32_t *__restrict__ labels,
+                           unsigned long long *__restrict__ unassigned) {
+    const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int x = -1;
+    if (a < n) {
+        if (resume) x = labels[a] >= 0 ? labels[a] : -1;
+        if (x < 0) {
+            const float *row = Y + a * L;
+            for (int t = 0; t < T; ++t) {
+                const int i = __ldg(plab + t);
+                if (row[i] > __ldg(pthr + t)) {
+                    x = i;
+                    break;
+                }
+            }
+        }
+        labels[a] = x;
+    }
+    if (unassigned) {
+        const unsigned m = __ballot_sync(0xffffffffu, a < n && x < 0);
+        if ((threadIdx.x & 31) == 0 && m) atomicAdd(unassigned, (unsigned long long)__popc(m));
+    }
+}
+
 __global__ void k_onehot(const int32_t *__restrict__ labels, int64_t n, int L, float *__restrict__ Y,
                          int *__restrict__ status) {
     const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1438,6 +1467,47 @@ extern "C" dcrf_status dcrf_round(const float *Y, int64_t n, int L, int32_t *lab
     cudaStream_t s = (cudaStream_t)stream;
     k_round<<<nblocks(n, 256), 256, 0, s>>>(Y, n, L, labels, onehot);
     DCRF_LAUNCHED();
+    return DCRF_OK;
+}
+
+extern "C" dcrf_status dcrf_round_kt(const float *Y, int64_t n, int L, int n_phases, const int32_t *phase_labels,
+                                     const float *phase_thresholds, int resume, int32_t *labels,
+                                     int64_t *unassigned, dcrf_stream stream) {
+    if (n < 0 || L < 1 || n_phases < 0 || (n > 0 && (!Y || !labels)) ||
+        (n_phases > 0 && (!phase_labels || !phase_thresholds)))
+        return DCRF_E_INVAL;
+    for (int t = 0; t < n_phases; ++t)
+        if (phase_labels[t] < 0 || phase_labels[t] >= L || !(phase_thresholds[t] >= 0.f) ||
+            !(phase_thresholds[t] < 1.f))
+            return DCRF_E_INVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) {
+        if (unassigned) *unassigned = 0;
+        return DCRF_OK;
+    }
+    Scratch sc(s);
+    int32_t *plab = nullptr;
+    float *pthr = nullptr;
+    unsigned long long *cnt = nullptr;
+    const int T = n_phases;
+    DCRF_CHECK_STATUS(sc.get(&plab, (size_t)(T > 0 ? T : 1)));
+    DCRF_CHECK_STATUS(sc.get(&pthr, (size_t)(T > 0 ? T : 1)));
+    if (T > 0) {
+        DCRF_TRY(cudaMemcpyAsync(plab, phase_labels, T * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        DCRF_TRY(cudaMemcpyAsync(pthr, phase_thresholds, T * sizeof(float), cudaMemcpyHostToDevice, s));
+    }
+    if (unassigned) {
+        DCRF_CHECK_STATUS(sc.get(&cnt, 1));
+        DCRF_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
+    }
+    k_round_kt<<<nblocks(n, 256), 256, 0, s>>>(Y, n, L, plab, pthr, T, resume, labels, cnt);
+    DCRF_LAUNCHED();
+    if (unassigned) {
+        unsigned long long h = 0;
+        DCRF_TRY(cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, s));
+        DCRF_TRY(cudaStreamSynchronize(s));
+        *unassigned = (int64_t)h;
+    }
     return DCRF_OK;
 }
 
