@@ -72,7 +72,8 @@ int dcrf_version(void);
 /*
  * Step a1 -- features of Appendix G (kernel form of Eq. 4).
  * rgb: device [N][3] float32, the images of the batch concatenated, each
- *   row-major (pixel a = y*W + x).  widths, heights: host [batch].
+ *   row-major (pixel a = y*W + x).  widths, heights: host [batch]; an image
+ *   may be empty (a width or height of 0).
  * f_bil: device [N][5] = (x/theta_alpha, y/theta_alpha, rgb/theta_beta).
  * f_sp:  device [N][2] = (x, y)/theta_gamma.  Either output may be NULL.
  * Each value is one correctly rounded float32 division.
@@ -168,6 +169,25 @@ dcrf_status dcrf_filter_adjoint(dcrf_lattice lat, const float *U, int L, float *
 dcrf_status dcrf_qp_fw(const float *unaries, const dcrf_lattice *lattices, const float *weights,
                        int n_kernels, const float *compat, int L, int iters, float *Y,
                        dcrf_fw_record *records, int storage, dcrf_stream stream);
+
+/*
+ * The whole QP path from host memory in one call: features (Eq. 4), the
+ * bilateral (d = 5) and spatial (d = 2) lattices, `iters` Frank-Wolfe
+ * iterations as dcrf_qp_fw, and y back to the host.
+ * rgb: host [N][3]; unaries: host [N][L]; Y0: host [N][L] (rows on the
+ * simplex); Y: host [N][L] output (may be Y0).  widths, heights: host
+ * [batch], N = sum of widths x heights.  thetas as dcrf_features; weights:
+ * host [2] (bilateral, spatial); compat, records and storage as dcrf_qp_fw.
+ * Device memory is taken from the stream-ordered allocator and released
+ * before the return.  The unaries and y0 upload on a second stream while the
+ * lattices are built; with page-locked host memory (cudaHostAlloc,
+ * cudaHostRegister) that upload overlaps the builds, with pageable memory it
+ * is synchronous.  Synchronises before returning; errors as the steps.
+ */
+dcrf_status dcrf_qp_fw_host(const float *rgb, const float *unaries, const float *Y0, float *Y,
+                            const int32_t *widths, const int32_t *heights, int batch, int L, float theta_alpha,
+                            float theta_beta, float theta_gamma, const float *weights, const float *compat,
+                            int iters, dcrf_fw_record *records, int storage, dcrf_stream stream);
 
 /*
  * Reverse mode through `iters` unrolled Frank-Wolfe iterations (the
@@ -312,6 +332,16 @@ dcrf_status dcrf_lp_solve_tree(const float *unaries, const dcrf_lattice *lattice
                                int n_kernels, int L, int n_subtrees, const uint64_t *subtree_labels,
                                const float *subtree_weights, int steps, double beta0, float *Y,
                                double *energies, dcrf_stream stream);
+
+/*
+ * Device scratch: every call takes its temporary device memory from a
+ * stream-ordered pool that the library keeps per device and that holds on to
+ * memory between calls (DCRF_POOL=default in the environment uses the
+ * device's default pool instead).  dcrf_pool_trim returns the pools' unused
+ * memory to the driver; call it once the streams that ran library calls are
+ * synchronised.
+ */
+dcrf_status dcrf_pool_trim(void);
 
 /*
  * Measurement hooks (no counterpart in the paper): when enabled, every

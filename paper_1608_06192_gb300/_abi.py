@@ -65,6 +65,8 @@ _SIGS = {
     "dcrf_lp_solve": ([_P, _P, _P, _I, _I, _I, _D, _P, _P, _P], _I),
     "dcrf_lp_subgrad_tree": ([_P, _P, _P, _P, _I, _I, _I, _P, _P, _P, _P, _P], _I),
     "dcrf_lp_solve_tree": ([_P, _P, _P, _I, _I, _I, _P, _P, _I, _D, _P, _P, _P], _I),
+    "dcrf_qp_fw_host": ([_P, _P, _P, _P, _P, _P, _I, _I, _F, _F, _F, _P, _P, _I, _P, _I, _P], _I),
+    "dcrf_pool_trim": ([], _I),
     "dcrf_round_kt": ([_P, _I64, _I, _I, _P, _P, _I, _P, _P, _P], _I),
     "dcrf_simplex_project": ([_P, _I64, _I, _P, _P], _I),
     "dcrf_profile_enable": ([_I], _I),
@@ -248,6 +250,51 @@ def dcrf_qp_fw(unaries: torch.Tensor, lattices, weights, Y: torch.Tensor, iters:
     return arr.reshape(iters, batch, 5)
 
 
+def _host(a, name: str, cols: int | None = None):
+    """A C-contiguous float32 host array (numpy, or a CPU tensor, pinned or not) and its address."""
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or a.dtype != torch.float32 or not a.is_contiguous():
+            raise ValueError(f"{name}: contiguous float32 host tensor required")
+        arr, ptr = a, ctypes.c_void_p(a.data_ptr())
+    else:
+        arr = np.asarray(a)
+        if arr.dtype != np.float32 or not arr.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{name}: C-contiguous float32 array required")
+        ptr = arr.ctypes.data_as(_P)
+    if arr.ndim != 2 or (cols is not None and arr.shape[1] != cols):
+        raise ValueError(f"{name}: shape [N, {cols if cols is not None else 'L'}] required")
+    return arr, ptr
+
+
+def dcrf_qp_fw_host(rgb, unaries, Y0, widths, heights, thetas, weights, iters: int, Y=None, compat=None,
+                    storage: str = "f16", records: bool = False, stream=None):
+    """The QP path from host buffers: features, both lattices, Frank-Wolfe, y back
+    in `Y` (a new numpy array unless given; may be Y0).  Returns (Y, records or None)."""
+    w = np.ascontiguousarray(np.asarray(widths, dtype=np.int32))
+    h = np.ascontiguousarray(np.asarray(heights, dtype=np.int32))
+    rgb, prgb = _host(rgb, "rgb", 3)
+    unaries, pphi = _host(unaries, "unaries")
+    L = unaries.shape[1]
+    Y0, py0 = _host(Y0, "Y0", L)
+    if Y is None:
+        Y = np.empty(tuple(Y0.shape), dtype=np.float32)
+    Y, py = _host(Y, "Y", L)
+    n = int((w.astype(np.int64) * h).sum())
+    if not (rgb.shape[0] == unaries.shape[0] == Y0.shape[0] == Y.shape[0] == n):
+        raise ValueError("rgb, unaries, Y0 and Y must have one row per pixel of the batch")
+    batch = len(w)
+    rec = (FwRecord * max(1, iters * batch))() if records else None
+    cm = _compat(compat, L)
+    ta, tb, tg = thetas
+    _check(lib().dcrf_qp_fw_host(prgb, pphi, py0, py, w.ctypes.data_as(_P), h.ctypes.data_as(_P), batch, L,
+                                 ta, tb, tg, _floats(weights), None if cm is None else cm[1], iters, rec,
+                                 STORAGE[storage], _stream(stream)), "dcrf_qp_fw_host")
+    if not records:
+        return Y, None
+    arr = np.array([(r.energy, r.gap, r.alpha, r.A, r.B) for r in rec[:iters * batch]], dtype=np.float64)
+    return Y, arr.reshape(iters, batch, 5)
+
+
 def dcrf_qp_fw_backward(unaries, lattices, weights, Y0, dYT, iters: int, compat=None, need_dy0: bool = False,
                         stream=None):
     """(dphi [N, L], dweights [n_kernels] float64, dY0 or None) of <dYT, y^T>."""
@@ -324,6 +371,11 @@ def dcrf_round(Y, onehot: bool = False, stream=None):
     _check(lib().dcrf_round(_ptr(Y), Y.shape[0], Y.shape[1], _ptr(labels), None if oh is None else _ptr(oh),
                             _stream(stream)), "dcrf_round")
     return (labels, oh) if onehot else labels
+
+
+def pool_trim():
+    """Return the library's unused cached device memory to the driver."""
+    _check(lib().dcrf_pool_trim(), "dcrf_pool_trim")
 
 
 def dcrf_round_kt(Y, phase_labels, phase_thresholds, labels=None, count: bool = True, stream=None):

@@ -89,11 +89,17 @@ std::vector<Chunk> make_chunks(const std::vector<int64_t> &off, int size);
 dcrf_status dcrf_check_lattices(const dcrf_lattice *lats, int n_k);
 int dcrf_round4(int L);
 
+// The library's caching pool for the stream's device (pool.cu), or NULL for
+// the default pool (while the stream is captured, or when DCRF_POOL=default).
+cudaMemPool_t dcrf_scratch_pool(cudaStream_t s);
+
 template <typename T>
 dcrf_status dcrf_alloc(T **p, size_t count, cudaStream_t s) {
     *p = nullptr;
     if (count == 0) return DCRF_OK;
-    cudaError_t e = cudaMallocAsync((void **)p, count * sizeof(T), s);
+    cudaMemPool_t pool = dcrf_scratch_pool(s);
+    cudaError_t e = pool ? cudaMallocFromPoolAsync((void **)p, count * sizeof(T), pool, s)
+                         : cudaMallocAsync((void **)p, count * sizeof(T), s);
     if (e != cudaSuccess) { *p = nullptr; return DCRF_E_NOMEM; }
     return DCRF_OK;
 }

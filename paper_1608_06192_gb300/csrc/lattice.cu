@@ -102,14 +102,16 @@ extern "C" dcrf_status dcrf_features(const float *rgb, const int32_t *widths, co
                                      int batch, float theta_alpha, float theta_beta,
                                      float theta_gamma, float *f_bil, float *f_sp,
                                      dcrf_stream stream) {
-    if (!rgb || !widths || !heights || batch < 1 || (!f_bil && !f_sp)) return DCRF_E_INVAL;
+    if (!widths || !heights || batch < 1 || (!f_bil && !f_sp)) return DCRF_E_INVAL;
     if (!(theta_alpha > 0.f) || !(theta_beta > 0.f) || !(theta_gamma > 0.f)) return DCRF_E_INVAL;
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<int64_t> off(batch + 1, 0);
     for (int b = 0; b < batch; ++b) {
-        if (widths[b] < 1 || heights[b] < 1) return DCRF_E_INVAL;
+        if (widths[b] < 0 || heights[b] < 0) return DCRF_E_INVAL;
         off[b + 1] = off[b] + (int64_t)widths[b] * heights[b];
     }
+    if (off[batch] == 0) return DCRF_OK;           // every image empty
+    if (!rgb) return DCRF_E_INVAL;
     Scratch sc(s);
     int64_t *off_d;
     int32_t *w_d;
