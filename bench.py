@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--height", type=int, default=375)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-all-cores", action="store_true")
     ap.add_argument("--no-lp", action="store_true")
     ap.add_argument("--no-dcneg", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the CCCP and reverse-mode timings")
@@ -115,6 +116,39 @@ def _oracle_rate(iters, seed):
     qp.frank_wolfe(c, p.y0, iters)
     dt = time.perf_counter() - t0
     return iters / dt, dt, 1
+
+
+def _oracle_worker(seed, iters, barrier, out):
+    """One process of the all-cores oracle timing: its own image, timed after a common start."""
+    from oracle import crf, qp
+    from oracle import permutohedral as P
+    p = S.make_problem(500, 375, 30, 21, seed)
+    fb, fs = crf.features(p.rgb, *p.thetas)
+    k = P.LatticeGaussian([crf.to_fp32_features(fb), crf.to_fp32_features(fs)], p.weights)
+    c = crf.DenseCRF(p.unaries, k)
+    qp.frank_wolfe(c, p.y0, 1)                      # warm-up
+    barrier.wait()
+    t0 = time.perf_counter()
+    qp.frank_wolfe(c, p.y0, iters)
+    out.put(time.perf_counter() - t0)
+
+
+def oracle_rate_all_cores(iters: int, workers: int):
+    """The oracle on every host core at once: one single-threaded process per
+    core, each on its own 500x375 image (the images are independent problems).
+    Returns (image-iterations/s over all processes, slowest process's seconds)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")                  # never fork a process that holds a CUDA context
+    barrier, out = ctx.Barrier(workers), ctx.SimpleQueue()
+    procs = [ctx.Process(target=_oracle_worker, args=(100 + w, iters, barrier, out)) for w in range(workers)]
+    for q in procs:
+        q.start()
+    for q in procs:
+        q.join(timeout=600)
+    if any(q.exitcode != 0 for q in procs):
+        return None, None
+    dts = [out.get() for _ in range(workers)]
+    return workers * iters / max(dts), max(dts)
 
 
 def workload_config(B, W, H, T, storage):
@@ -524,6 +558,13 @@ def main():
         cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "20 oracle Frank-Wolfe iterations on one 500x375 image (FP64 numpy)",
                "seconds": round(dt, 2)}
+        workers = os.cpu_count() or 1
+        if workers > 1 and not args.no_cpu_all_cores:
+            ra, dta = oracle_rate_all_cores(5, workers)
+            if ra is not None:
+                cpu["all_cores"] = {"value": ra, "unit": UNIT, "cores": workers,
+                                    "sample": "%d processes, one per core, 5 oracle Frank-Wolfe iterations each on "
+                                              "its own 500x375 image" % workers, "seconds": round(dta, 2)}
 
     if rank == 0:
         line = {

@@ -86,3 +86,10 @@ def test_reference_arm_line_matches_the_gpu_arm_config():
     assert line["config"] == bench.workload_config(2, 500, 375, 100, "f16")
     assert line["metric"] == bench.METRIC and line["higher_is_better"] is True
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_all_cores_oracle_timing_spawns_one_process_per_core():
+    import bench
+    rate, slowest = bench.oracle_rate_all_cores(1, 2)
+    assert rate is not None and slowest > 0
+    assert rate == pytest.approx(2 / slowest)
