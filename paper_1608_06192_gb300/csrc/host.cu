@@ -5,13 +5,16 @@
 //   1. upload the RGB images (small: 12 bytes a pixel);
 //   2. features (Eq. 4 in kernel form) and the bilateral and spatial
 //      lattices (Section 3), whose builds read counts back to the host;
-//   3. meanwhile a second stream uploads the unaries and y0 (8L bytes a
-//      pixel, the bulk of the input), so the copy engine works while the
-//      lattices are built;
+//   3. meanwhile, once the images have landed, a second stream uploads the
+//      unaries and y0 (8L bytes a pixel, the bulk of the input), so the copy
+//      engine works while the lattices are built;
 //   4. Frank-Wolfe (Algorithm 1 with the closed-form step of Appendix B),
 //      once both uploads have landed;
 //   5. download y and synchronise.
 // With pageable host memory the uploads still work but no longer overlap.
+#include <cstdio>
+#include <cstdlib>
+
 #include "common.cuh"
 
 namespace {
@@ -30,6 +33,36 @@ struct EventGuard {
     cudaEvent_t e = nullptr;
     ~EventGuard() {
         if (e) cudaEventDestroy(e);
+    }
+};
+
+// DCRF_HOST_LOG=1: CUDA events at the phase boundaries, printed to stderr
+// as milliseconds after the call's start once the call has synchronised.
+struct PhaseLog {
+    static constexpr int kMax = 8;
+    bool on = false;
+    int n = 0;
+    cudaEvent_t ev[kMax] = {};
+    const char *name[kMax] = {};
+    PhaseLog() {
+        const char *e = std::getenv("DCRF_HOST_LOG");
+        on = e && e[0] == '1';
+    }
+    void mark(const char *what, cudaStream_t st) {
+        if (!on || n >= kMax) return;
+        if (cudaEventCreate(&ev[n]) != cudaSuccess) return;
+        cudaEventRecord(ev[n], st);
+        name[n++] = what;
+    }
+    void print() {
+        for (int i = 1; i < n; ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[0], ev[i]);
+            std::fprintf(stderr, "dcrf host: %-22s %8.3f ms\n", name[i], ms);
+        }
+    }
+    ~PhaseLog() {
+        for (int i = 0; i < n; ++i) cudaEventDestroy(ev[i]);
     }
 };
 
@@ -64,6 +97,8 @@ extern "C" dcrf_status dcrf_qp_fw_host(const float *rgb, const float *unaries, c
     LatticeGuard lg;
     EventGuard ready, landed;
     StreamGuard up;
+    PhaseLog log;
+    log.mark("start", s);
 
     const size_t nn = (size_t)(n > 0 ? n : 1);
     float *rgb_d, *fb, *fs, *phi_d, *y_d;
@@ -76,25 +111,33 @@ extern "C" dcrf_status dcrf_qp_fw_host(const float *rgb, const float *unaries, c
     DCRF_TRY(cudaEventCreateWithFlags(&landed.e, cudaEventDisableTiming));
     DCRF_TRY(cudaStreamCreateWithFlags(&up.s, cudaStreamNonBlocking));
 
-    // the buffers exist (stream-ordered allocation on s) before the upload
-    // stream writes them
+    // the images go first: copies in one direction share the copy engine, and
+    // the builds wait for the images only.  The upload stream starts once the
+    // buffers exist (stream-ordered allocation on s) and the images have landed.
+    if (n > 0) DCRF_TRY(cudaMemcpyAsync(rgb_d, rgb, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, s));
+    log.mark("rgb uploaded", s);
     DCRF_TRY(cudaEventRecord(ready.e, s));
     DCRF_TRY(cudaStreamWaitEvent(up.s, ready.e, 0));
     if (n > 0) {
         DCRF_TRY(cudaMemcpyAsync(phi_d, unaries, (size_t)n * L * sizeof(float), cudaMemcpyHostToDevice, up.s));
         DCRF_TRY(cudaMemcpyAsync(y_d, Y0, (size_t)n * L * sizeof(float), cudaMemcpyHostToDevice, up.s));
-        DCRF_TRY(cudaMemcpyAsync(rgb_d, rgb, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, s));
     }
     DCRF_TRY(cudaEventRecord(landed.e, up.s));
+    log.mark("unaries+y0 uploaded", up.s);
 
     DCRF_CHECK_STATUS(dcrf_features(rgb_d, widths, heights, batch, theta_alpha, theta_beta, theta_gamma, fb, fs,
                                     stream));
     DCRF_CHECK_STATUS(dcrf_lattice_build_batch(fb, off.data(), batch, 5, stream, &lg.l[0]));
     DCRF_CHECK_STATUS(dcrf_lattice_build_batch(fs, off.data(), batch, 2, stream, &lg.l[1]));
+    log.mark("lattices built", s);
 
     DCRF_TRY(cudaStreamWaitEvent(s, landed.e, 0));
+    log.mark("solver starts", s);
     DCRF_CHECK_STATUS(dcrf_qp_fw(phi_d, lg.l, weights, 2, compat, L, iters, y_d, records, storage, stream));
+    log.mark("solver done", s);
     if (n > 0) DCRF_TRY(cudaMemcpyAsync(Y, y_d, (size_t)n * L * sizeof(float), cudaMemcpyDeviceToHost, s));
+    log.mark("y downloaded", s);
     DCRF_TRY(cudaStreamSynchronize(s));
+    log.print();
     return DCRF_OK;
 }
