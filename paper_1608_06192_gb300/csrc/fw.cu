@@ -149,6 +149,103 @@ __global__ void __launch_bounds__(256) k_fw_blur(BlurSet B, int p) {
     }
 }
 
+// Persistent blur pass: a grid of resident blocks strides over the vertex
+// rows, and every thread loads the neighbour pair of its next row while it
+// works on the current one, so a row waits for one round trip to memory
+// (its three rows) instead of two (the pair, then the rows).  Same
+// arithmetic as k_fw_blur.
+template <int LP, typename T>
+__device__ __forceinline__ bool blur2_locate(const BlurSet &B, int p, int64_t g, BlurLat &lt, int64_t &v) {
+    int mm = 0;
+#pragma unroll
+    for (int k = 1; k < DCRF_MAX_KERNELS; ++k)
+        if (k < B.nk && g >= B.start[k]) mm = k;
+    lt = B.l[0];
+#pragma unroll
+    for (int k = 1; k < DCRF_MAX_KERNELS; ++k)
+        if (k == mm) lt = B.l[k];
+    v = g - B.start[mm];
+    return p < lt.d1;
+}
+
+template <int LP, typename T>
+__global__ void __launch_bounds__(256) k_fw_blur2(BlurSet B, int p, int64_t work) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    BlurLat lt;
+    int64_t v = 0;
+    bool live = g < work && blur2_locate<LP, T>(B, p, g, lt, v);
+    int2 nb = live ? reinterpret_cast<const int2 *>(lt.nbr)[v * lt.d1 + p] : make_int2(-1, -1);
+    while (g < work) {
+        // the next row's lattice, vertex and neighbour pair, in flight during this row
+        const int64_t gn = g + stride;
+        BlurLat ln;
+        int64_t vn = 0;
+        const bool live_n = gn < work && blur2_locate<LP, T>(B, p, gn, ln, vn);
+        const int2 nbn = live_n ? reinterpret_cast<const int2 *>(ln.nbr)[vn * ln.d1 + p] : make_int2(-1, -1);
+        if (live) {
+            const int D = lt.d1 - 1;
+            T *out = ((D - p) % 2 == 0) ? (T *)lt.dst : (T *)lt.tmp;
+            bool done = false;
+            if constexpr (sizeof(T) == 2 && LP <= 24) {
+                if (p > 0) {
+                    const uint4 *in = reinterpret_cast<const uint4 *>(((D - p + 1) % 2 == 0) ? lt.dst : lt.tmp);
+                    uint4 c[LP / 8], a[LP / 8], b[LP / 8];
+                    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                    for (int q = 0; q < LP / 8; ++q) {
+                        c[q] = in[v * (LP / 8) + q];
+                        a[q] = nb.x >= 0 ? in[(int64_t)nb.x * (LP / 8) + q] : z;
+                        b[q] = nb.y >= 0 ? in[(int64_t)nb.y * (LP / 8) + q] : z;
+                    }
+#pragma unroll
+                    for (int q = 0; q < LP / 8; ++q) {
+                        const __half2 *hc = reinterpret_cast<const __half2 *>(&c[q]);
+                        const __half2 *ha = reinterpret_cast<const __half2 *>(&a[q]);
+                        const __half2 *hb = reinterpret_cast<const __half2 *>(&b[q]);
+                        float o[8];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const float2 fc = __half22float2(hc[j]), fa = __half22float2(ha[j]);
+                            const float2 fb = __half22float2(hb[j]);
+                            o[2 * j] = 0.5f * fc.x + 0.25f * fa.x + 0.25f * fb.x;
+                            o[2 * j + 1] = 0.5f * fc.y + 0.25f * fa.y + 0.25f * fb.y;
+                        }
+                        row_store(out, v, LP, q, o);
+                    }
+                    done = true;
+                }
+            }
+            if (!done) {
+#pragma unroll
+                for (int q = 0; q < LP / 8; ++q) {
+                    float c[8], a[8], b[8];
+                    if (p == 0) {
+                        row_load<float>(lt.src0, v, LP, q, c);
+                        if (nb.x >= 0) row_load<float>(lt.src0, nb.x, LP, q, a);
+                        if (nb.y >= 0) row_load<float>(lt.src0, nb.y, LP, q, b);
+                    } else {
+                        const T *in = ((D - p + 1) % 2 == 0) ? (const T *)lt.dst : (const T *)lt.tmp;
+                        row_load<T>(in, v, LP, q, c);
+                        if (nb.x >= 0) row_load<T>(in, nb.x, LP, q, a);
+                        if (nb.y >= 0) row_load<T>(in, nb.y, LP, q, b);
+                    }
+                    float o[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        o[j] = 0.5f * c[j] + (nb.x >= 0 ? 0.25f * a[j] : 0.f) + (nb.y >= 0 ? 0.25f * b[j] : 0.f);
+                    row_store(out, v, LP, q, o);
+                }
+            }
+        }
+        g = gn;
+        lt = ln;
+        v = vn;
+        live = live_n;
+        nb = nbn;
+    }
+}
+
 // Label-split blur pass: LP / 8 lanes per vertex row, lane q owning labels
 // 8q .. 8q+7, so that a warp instruction reads whole rows (own and both
 // neighbours) instead of one 16-byte piece of 32 rows; a warp holds
@@ -790,6 +887,10 @@ struct Solver {
                 constexpr int RW = 32 / (LPc / 8);
                 const int64_t warps = (work + RW - 1) / RW;
                 k_fw_blur3<LPc, T><<<nblocks(warps * 32, 256), 256, 0, s>>>(B, p);
+            } else if (variant_ == 2) {
+                const int64_t full = (work + 255) / 256;
+                const int64_t grid = std::min<int64_t>(full, (int64_t)resident_blocks<LPc, T>());
+                k_fw_blur2<LPc, T><<<(unsigned)grid, 256, 0, s>>>(B, p, work);
             } else {
                 k_fw_blur<LPc, T><<<nblocks(work, 256), 256, 0, s>>>(B, p);
             }
@@ -798,13 +899,29 @@ struct Solver {
         return DCRF_OK;
     }
 
-    // Blur tuner: a vertex row per thread (0) or label-split rows (1), timed on
+    // Blocks of k_fw_blur2 that fit on the device at once (SMs x resident blocks per SM).
+    template <int LPc, typename T>
+    int resident_blocks() {
+        static int cached = 0;
+        if (cached > 0) return cached;
+        int dev = 0, sms = 1, per_sm = 1;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fw_blur2<LPc, T>, 256, 0) != cudaSuccess)
+            return 1024;
+        cached = std::max(1, sms * std::max(1, per_sm));
+        return cached;
+    }
+
+    // Blur tuner: a vertex row per thread (0), label-split rows (1) or the
+    // persistent form with the neighbour pair loaded a row ahead (2), timed on
     // this problem's lattices (the blur only reads Slat and writes BS and tmp,
     // which every iteration overwrites) and cached per (Lp, storage, size bucket).
     template <int LPc, typename T>
     dcrf_status tune_blur(const BlurSet &B, int dmax) {
         if (const char *force = std::getenv("DCRF_BLUR_VARIANT")) {   // testing hook
-            blur_variant = std::atoi(force) == 1 ? 1 : 0;
+            const int f = std::atoi(force);
+            blur_variant = (f == 1 || f == 2) ? f : 0;
             return DCRF_OK;
         }
         static std::mutex mu_;
@@ -826,7 +943,7 @@ struct Solver {
         DCRF_TRY(cudaEventCreate(&e1));
         float best = 1e30f;
         int arg = 0;
-        for (int v = 0; v < 2; ++v) {
+        for (int v = 0; v < 3; ++v) {
             DCRF_CHECK_STATUS((blur_passes<LPc, T>(B, dmax, v)));   // warm-up
             DCRF_TRY(cudaEventRecord(e0, s));
             for (int r = 0; r < 3; ++r) DCRF_CHECK_STATUS((blur_passes<LPc, T>(B, dmax, v)));

@@ -157,13 +157,30 @@ def test_fw_bulk_variant_on_unaligned_batch(dcrf, variant, monkeypatch):
         _check_against_oracle(probs, g, Y, rec, 12, mono=1e-6 if storage == "f32" else 1e-4)
 
 
-@pytest.mark.parametrize("blur", [0, 1])
+@pytest.mark.parametrize("blur", [0, 1, 2])
 @pytest.mark.parametrize("L", [5, 21, 40])
 def test_fw_each_blur_kernel(dcrf, blur, L, monkeypatch):
-    # the blur tuner chooses a row per thread (0) or label-split rows (1); both
-    # follow the oracle for 8-, 24- and 64-wide rows
+    # the blur tuner chooses a row per thread (0), label-split rows (1) or the
+    # persistent form (2); each follows the oracle for 8-, 24- and 64-wide rows
     monkeypatch.setenv("DCRF_BLUR_VARIANT", str(blur))
     p = S.make_problem(64, 48, 6, L, seed=80 + L)
     for storage in ("f32", "f16"):
         g, Y, rec = _run_fw(dcrf, [p], 10, storage=storage)
         _check_against_oracle([p], g, Y, rec, 10, mono=1e-6 if storage == "f32" else 1e-4)
+
+
+def test_fw_persistent_blur_strides_over_many_rows(dcrf, monkeypatch):
+    # 10 images of 500x375: ~460k vertex rows, more than one row per thread of
+    # the persistent blur's resident grid; two sampled images follow the oracle
+    monkeypatch.setenv("DCRF_BLUR_VARIANT", "2")
+    B, iters = 10, 6
+    probs = [S.make_problem(500, 375, 30, 21, seed=200 + i) for i in range(B)]
+    g = gpu_setup(dcrf, probs, torch)
+    assert g["lb"].m + g["ls"].m > 152 * 8 * 256
+    Y = g["y0"].clone()
+    rec = dcrf.dcrf_qp_fw(g["phi"], [g["lb"], g["ls"]], probs[0].weights, Y, iters, storage="f16")
+    for b in (0, B - 1):
+        c = oracle_crf(probs[b])
+        _, _, rec_o = qp.frank_wolfe(c, probs[b].y0, iters)
+        scale = np.abs(rec_o[:, 0]).max()
+        assert np.abs(rec[:, b, 0] - rec_o[:, 0]).max() <= 1e-3 * scale
