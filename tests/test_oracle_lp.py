@@ -252,3 +252,27 @@ def test_tree_lp_objective_euler_identity_subgradient_and_integer_points():
     E = np.sum(phi[np.arange(n), x]) + sum(Kd[a, b] * _tree_distance(x[a], x[b]) / 2.0
                                            for a in range(n) for b in range(n) if a != b)
     np.testing.assert_allclose(lp.s_lp_tree_pairs(phi, Kd, Y, members, c_t), E, rtol=1e-12)
+
+
+@pytest.mark.parametrize("L", [2, 5, 21, 64])
+def test_synthetic_hst_tree_is_a_tree(L):
+    # the benchmark's tree: subtrees nest or are disjoint, every label is a
+    # leaf, and the path length between labels (the sum of c_T over the
+    # subtrees holding exactly one of them) is a metric; at L = 21 it is 2
+    # between siblings of a group, 6 across groups of a half and 14 across
+    # halves (edges of length 1, 2 and 4)
+    from paper_1608_06192_gb300 import synthetic as S
+    members, c_t = S.hst_tree(L)
+    sets = [frozenset(np.nonzero(m)[0]) for m in members]
+    for a in sets:
+        for b in sets:
+            assert a <= b or b <= a or not (a & b)
+    assert all(frozenset([i]) in sets for i in range(L))
+    D = np.array([[sum(c for t, c in zip(sets, c_t) if (i in t) != (j in t)) for j in range(L)] for i in range(L)])
+    assert np.all(D == D.T) and np.all(np.diag(D) == 0) and np.all(D + np.eye(L) > 0)
+    for i in range(L):
+        for j in range(L):
+            for k in range(L):
+                assert D[i, k] <= D[i, j] + D[j, k]
+    if L == 21:
+        assert D[0, 1] == 2 and D[0, 4] == 6 and D[0, 20] == 14 and D[10, 13] == 2 and D[10, 14] == 6
