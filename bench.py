@@ -6,10 +6,12 @@ regions), lattices built beforehand (they are reused by every iteration), with
 float16 lattice storage.  value = images x iterations / second over all ranks.
 
 Also reported: the plain float32 single-image form, the end-to-end rate
-through the public API from host buffers (features, lattice builds, solver and
-copies inside the timed region), the roofline of the dominant kernel from CUDA
-events taken on the launching stream inside the timed region, the oracle timed
-on the host cores, and SM clocks sampled during the timed region.
+through the C ABI's host-buffer call dcrf_qp_fw_host (uploads, features,
+lattice builds, solver and download inside the timed region), the roofline of
+the dominant kernel from CUDA events taken on the launching stream in a second
+pass over the same steps (the first, un-instrumented pass gives `value`), the
+oracle timed on one host core and on all of them, and SM clocks sampled during
+the timed region.
 
 Multi-GPU: one process per GPU (torchrun); every rank solves its own batch
 (images are independent problems), so there is no data-path collective; only
