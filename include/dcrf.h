@@ -171,6 +171,19 @@ dcrf_status dcrf_qp_fw(const float *unaries, const dcrf_lattice *lattices, const
                        dcrf_fw_record *records, int storage, dcrf_stream stream);
 
 /*
+ * dcrf_qp_fw that also returns the solver's decisions: s_trace, device uint8
+ * [iters][N], receives in row t the conditional gradient s^t = argmin_i g_a(i)
+ * of iteration t for every pixel (Eq. 14; row 0 is the argmin at y^0).  The
+ * rows make a run reproducible outside the library: replaying them through
+ * Algorithm 1 with the closed-form step of Appendix B retraces y^t exactly up
+ * to rounding, also where an argmin is within rounding of a tie.  s_trace may
+ * be NULL (then this is dcrf_qp_fw).  Costs one copy of N bytes per iteration.
+ */
+dcrf_status dcrf_qp_fw_trace(const float *unaries, const dcrf_lattice *lattices, const float *weights,
+                             int n_kernels, const float *compat, int L, int iters, float *Y,
+                             dcrf_fw_record *records, uint8_t *s_trace, int storage, dcrf_stream stream);
+
+/*
  * The whole QP path from host memory in one call: features (Eq. 4), the
  * bilateral (d = 5) and spatial (d = 2) lattices, `iters` Frank-Wolfe
  * iterations as dcrf_qp_fw, and y back to the host.
@@ -200,11 +213,14 @@ dcrf_status dcrf_qp_fw_host(const float *rgb, const float *unaries, const float 
  * iteration.  s^t is piecewise constant and alpha is constant where it is
  * clipped to [0, 1]; elsewhere alpha = -B/(2A) is differentiated exactly,
  * with Op^T applied through dcrf_filter_adjoint's reverse blur.
+ * s_tape: device uint8 [iters][N] or NULL: the recomputed forward's
+ * decisions s^t (as dcrf_qp_fw_trace), i.e. the smooth piece of the unrolled
+ * map whose derivative was taken.
  */
 dcrf_status dcrf_qp_fw_backward(const float *unaries, const dcrf_lattice *lattices, const float *weights,
                                 int n_kernels, const float *compat, int L, int iters, const float *Y0,
                                 const float *dYT, float *dphi, float *dY0, double *dweights,
-                                dcrf_stream stream);
+                                uint8_t *s_tape, dcrf_stream stream);
 
 /*
  * CCCP on the generic DC relaxation (Section 5.1, Algorithm 2): outer steps

@@ -36,16 +36,24 @@ def step_size(A: float, B: float) -> float:
     return 1.0 if A + B < 0.0 else 0.0
 
 
-def frank_wolfe(crf, y0, iters: int, lin=None, P_y=None):
-    """Returns (y, P_y, records); records[t] = (energy, gap, alpha, A, B) at y^t."""
+def frank_wolfe(crf, y0, iters: int, lin=None, P_y=None, decisions=None, on_step=None):
+    """Returns (y, P_y, records); records[t] = (energy, gap, alpha, A, B) at y^t.
+
+    decisions: optional [iters][n] label indices to use as s^t instead of the
+    argmin (a replay of another run's choices, which may differ from the FP64
+    argmin only where g is within rounding of a tie); on_step(t, g, s_idx) is
+    called with the gradient of every iteration and the vertex taken.
+    """
     lin = crf.phi - crf.d if lin is None else lin
     y = np.array(y0, dtype=np.float64)
     P_y = crf.psi_plus_D(y) if P_y is None else P_y.copy()
     rows = np.arange(crf.n)
     recs = []
-    for _ in range(iters):
+    for t in range(iters):
         g = lin + 2.0 * P_y
-        s_idx = np.argmin(g, axis=1)
+        s_idx = np.argmin(g, axis=1) if decisions is None else np.asarray(decisions[t], dtype=np.int64)
+        if on_step is not None:
+            on_step(t, g, s_idx)
         s = np.zeros_like(y)
         s[rows, s_idx] = 1.0
         gap = float(np.sum(g * (y - s)))
@@ -188,17 +196,22 @@ class WeightedCRF:
     psi_plus_D = op
 
 
-def fw_tape(crf, y0, iters):
-    """Forward pass keeping y^t, s^t and (alpha, A, B) of every iteration."""
+def fw_tape(crf, y0, iters, decisions=None):
+    """Forward pass keeping y^t, s^t and (alpha, A, B) of every iteration.
+
+    decisions: optional [iters][n] label indices taken as s^t instead of the
+    argmin, which fixes the smooth piece of the unrolled map (see frank_wolfe).
+    """
     lin = crf.phi - crf.d
     y = np.array(y0, dtype=np.float64)
     P = crf.op(y)
     rows = np.arange(crf.n)
     tape = []
-    for _ in range(iters):
+    for t in range(iters):
         g = lin + 2.0 * P
         s = np.zeros_like(y)
-        s[rows, np.argmin(g, axis=1)] = 1.0
+        s_idx = np.argmin(g, axis=1) if decisions is None else np.asarray(decisions[t], dtype=np.int64)
+        s[rows, s_idx] = 1.0
         Ps = crf.op(s)
         delta, dP = s - y, Ps - P
         A = float(np.sum(delta * dP))

@@ -60,7 +60,8 @@ _SIGS = {
     "dcrf_mean_field": ([_P, _P, _P, _I, _P, _I, _I, _P, _P, _I, _P], _I),
     "dcrf_round": ([_P, ctypes.c_int64, _I, _P, _P, _P], _I),
     "dcrf_labelling_energy": ([_P, _P, _P, _I, _P, _I, _P, _P, _I, _P], _I),
-    "dcrf_qp_fw_backward": ([_P, _P, _P, _I, _P, _I, _I, _P, _P, _P, _P, _P, _P], _I),
+    "dcrf_qp_fw_trace": ([_P, _P, _P, _I, _P, _I, _I, _P, _P, _P, _I, _P], _I),
+    "dcrf_qp_fw_backward": ([_P, _P, _P, _I, _P, _I, _I, _P, _P, _P, _P, _P, _P, _P], _I),
     "dcrf_lp_subgrad": ([_P, _P, _P, _P, _I, _I, _P, _P, _P], _I),
     "dcrf_lp_solve": ([_P, _P, _P, _I, _I, _I, _D, _P, _P, _P], _I),
     "dcrf_lp_subgrad_tree": ([_P, _P, _P, _P, _I, _I, _I, _P, _P, _P, _P, _P], _I),
@@ -250,6 +251,24 @@ def dcrf_qp_fw(unaries: torch.Tensor, lattices, weights, Y: torch.Tensor, iters:
     return arr.reshape(iters, batch, 5)
 
 
+def dcrf_qp_fw_trace(unaries: torch.Tensor, lattices, weights, Y: torch.Tensor, iters: int, compat=None,
+                     storage: str = "f32", stream=None):
+    """dcrf_qp_fw that also returns the decisions: (records [iters, batch, 5],
+    s_trace uint8 [iters, N] on the device, row t = s^t of iteration t)."""
+    unaries = _dev(unaries, torch.float32, "unaries", 2)
+    Y = _dev(Y, torch.float32, "Y", 2)
+    L = unaries.shape[1]
+    batch = lattices[0].batch
+    rec = (FwRecord * max(1, iters * batch))()
+    trace = torch.empty((iters, Y.shape[0]), dtype=torch.uint8, device=Y.device)
+    cm = _compat(compat, L)
+    _check(lib().dcrf_qp_fw_trace(_ptr(unaries), _handles(lattices), _floats(weights), len(lattices),
+                                  None if cm is None else cm[1], L, iters, _ptr(Y), rec, _ptr(trace),
+                                  STORAGE[storage], _stream(stream)), "dcrf_qp_fw_trace")
+    arr = np.array([(r.energy, r.gap, r.alpha, r.A, r.B) for r in rec[:iters * batch]], dtype=np.float64)
+    return arr.reshape(iters, batch, 5), trace
+
+
 def _host(a, name: str, cols: int | None = None):
     """A C-contiguous float32 host array (numpy, or a CPU tensor, pinned or not) and its address."""
     if isinstance(a, torch.Tensor):
@@ -296,8 +315,9 @@ def dcrf_qp_fw_host(rgb, unaries, Y0, widths, heights, thetas, weights, iters: i
 
 
 def dcrf_qp_fw_backward(unaries, lattices, weights, Y0, dYT, iters: int, compat=None, need_dy0: bool = False,
-                        stream=None):
-    """(dphi [N, L], dweights [n_kernels] float64, dY0 or None) of <dYT, y^T>."""
+                        tape: bool = False, stream=None):
+    """(dphi [N, L], dweights [n_kernels] float64, dY0 or None) of <dYT, y^T>;
+    with tape=True a fourth item, the recomputed forward's decisions uint8 [iters, N]."""
     unaries = _dev(unaries, torch.float32, "unaries", 2)
     Y0 = _dev(Y0, torch.float32, "Y0", 2)
     dYT = _dev(dYT, torch.float32, "dYT", 2)
@@ -305,11 +325,13 @@ def dcrf_qp_fw_backward(unaries, lattices, weights, Y0, dYT, iters: int, compat=
     dphi = torch.empty_like(unaries)
     dy0 = torch.empty_like(Y0) if need_dy0 else None
     dw = np.zeros(len(lattices), dtype=np.float64)
+    st = torch.empty((iters, Y0.shape[0]), dtype=torch.uint8, device=Y0.device) if tape else None
     cm = _compat(compat, L)
     _check(lib().dcrf_qp_fw_backward(_ptr(unaries), _handles(lattices), _floats(weights), len(lattices),
                                      None if cm is None else cm[1], L, iters, _ptr(Y0), _ptr(dYT), _ptr(dphi),
-                                     _ptr(dy0), dw.ctypes.data_as(_P), _stream(stream)), "dcrf_qp_fw_backward")
-    return dphi, dw, dy0
+                                     _ptr(dy0), dw.ctypes.data_as(_P), _ptr(st), _stream(stream)),
+           "dcrf_qp_fw_backward")
+    return (dphi, dw, dy0, st) if tape else (dphi, dw, dy0)
 
 
 def dcrf_dc_cccp(unaries, lattices, weights, Y, outer: int, inner: int, compat=None, storage="f32",

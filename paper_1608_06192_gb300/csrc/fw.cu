@@ -31,7 +31,7 @@ namespace {
 
 // Blur pass `p` of every lattice in one launch (lattice m takes part while
 // p < d_m + 1): out[v] = in[v]/2 + (in[v - w_p] + in[v + w_p])/4 on whole rows
-// of LP labels, one thread per vertex.  Pass 0 reads the float32 splat Slat;
+// of LP labels, one thread per vertex.  Pass 0 reads the fixed-point splat Sq;
 // the last pass of lattice m lands in BS, earlier ones alternate with tmp.
 template <typename T>
 __device__ __forceinline__ void row_load(const T *p, int64_t v, int LP, int q, float (&o)[8]);
@@ -49,6 +49,13 @@ __device__ __forceinline__ void row_load<__half>(const __half *p, int64_t v, int
     const float2 c = __half22float2(*reinterpret_cast<const __half2 *>(&raw.z));
     const float2 d = __half22float2(*reinterpret_cast<const __half2 *>(&raw.w));
     o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y; o[4] = c.x; o[5] = c.y; o[6] = d.x; o[7] = d.y;
+}
+// Eight labels of a fixed-point splat row, as values: u * inv (inv = 2^-k).
+__device__ __forceinline__ void row_load_q(const uint32_t *p, int64_t v, int LP, int q, float inv, float (&o)[8]) {
+    const uint4 *r = reinterpret_cast<const uint4 *>(p + v * LP + 8 * q);
+    const uint4 a = r[0], b = r[1];
+    o[0] = (float)a.x * inv; o[1] = (float)a.y * inv; o[2] = (float)a.z * inv; o[3] = (float)a.w * inv;
+    o[4] = (float)b.x * inv; o[5] = (float)b.y * inv; o[6] = (float)b.z * inv; o[7] = (float)b.w * inv;
 }
 __device__ __forceinline__ void row_store(float *p, int64_t v, int LP, int q, const float (&o)[8]) {
     float4 *r = reinterpret_cast<float4 *>(p + v * LP + 8 * q);
@@ -68,7 +75,8 @@ __device__ __forceinline__ void row_store(__half *p, int64_t v, int LP, int q, c
 
 struct BlurLat {
     const int32_t *nbr;
-    const float *src0;   // Slat (float32) for pass 0
+    const uint32_t *src0;   // Sq (fixed point) for pass 0
+    const float *qs;        // its scales {2^k, 2^-k}
     void *dst;           // BS
     void *tmp;
     int64_t m;
@@ -132,9 +140,10 @@ __global__ void __launch_bounds__(256) k_fw_blur(BlurSet B, int p) {
     for (int q = 0; q < LP / 8; ++q) {
         float c[8], a[8], b[8];
         if (p == 0) {
-            row_load<float>(lt.src0, v, LP, q, c);
-            if (nb.x >= 0) row_load<float>(lt.src0, nb.x, LP, q, a);
-            if (nb.y >= 0) row_load<float>(lt.src0, nb.y, LP, q, b);
+            const float inv = __ldg(lt.qs + 1);
+            row_load_q(lt.src0, v, LP, q, inv, c);
+            if (nb.x >= 0) row_load_q(lt.src0, nb.x, LP, q, inv, a);
+            if (nb.y >= 0) row_load_q(lt.src0, nb.y, LP, q, inv, b);
         } else {
             const T *in = ((D - p + 1) % 2 == 0) ? (const T *)lt.dst : (const T *)lt.tmp;
             row_load<T>(in, v, LP, q, c);
@@ -221,9 +230,10 @@ __global__ void __launch_bounds__(256) k_fw_blur2(BlurSet B, int p, int64_t work
                 for (int q = 0; q < LP / 8; ++q) {
                     float c[8], a[8], b[8];
                     if (p == 0) {
-                        row_load<float>(lt.src0, v, LP, q, c);
-                        if (nb.x >= 0) row_load<float>(lt.src0, nb.x, LP, q, a);
-                        if (nb.y >= 0) row_load<float>(lt.src0, nb.y, LP, q, b);
+                        const float inv = __ldg(lt.qs + 1);
+                        row_load_q(lt.src0, v, LP, q, inv, c);
+                        if (nb.x >= 0) row_load_q(lt.src0, nb.x, LP, q, inv, a);
+                        if (nb.y >= 0) row_load_q(lt.src0, nb.y, LP, q, inv, b);
                     } else {
                         const T *in = ((D - p + 1) % 2 == 0) ? (const T *)lt.dst : (const T *)lt.tmp;
                         row_load<T>(in, v, LP, q, c);
@@ -275,9 +285,10 @@ __global__ void __launch_bounds__(256) k_fw_blur3(BlurSet B, int p) {
     const int2 nb = reinterpret_cast<const int2 *>(lt.nbr)[v * lt.d1 + p];
     float c[8], a[8], b[8];
     if (p == 0) {
-        row_load<float>(lt.src0, v, LP, q, c);
-        if (nb.x >= 0) row_load<float>(lt.src0, nb.x, LP, q, a);
-        if (nb.y >= 0) row_load<float>(lt.src0, nb.y, LP, q, b);
+        const float inv = __ldg(lt.qs + 1);
+        row_load_q(lt.src0, v, LP, q, inv, c);
+        if (nb.x >= 0) row_load_q(lt.src0, nb.x, LP, q, inv, a);
+        if (nb.y >= 0) row_load_q(lt.src0, nb.y, LP, q, inv, b);
     } else {
         const T *in = ((D - p + 1) % 2 == 0) ? (const T *)lt.dst : (const T *)lt.tmp;
         row_load<T>(in, v, LP, q, c);
@@ -294,6 +305,7 @@ __global__ void __launch_bounds__(256) k_fw_blur3(BlurSet B, int p) {
 // Lattice dot products for the line search:
 //   0: w s0 sum_v sum_ij mu_ij Ylat[v][i] BS[v][j]   (= <y, K~-part of Psi s>)
 //   1: w s0 sum_v sum_ij mu_ij Slat[v][i] BS[v][j]   (= <s, K~-part of Psi s>)
+// with Slat = Sq 2^-k the value of the fixed-point splat of s;
 // summed per warp in FP32.
 struct DotArgs {
     const Chunk *chunks;    // vertex chunks of lattice `which`
@@ -309,11 +321,12 @@ __global__ void __launch_bounds__(kVertBlock) k_fw_latdot(DotArgs A, FwLat lt) {
     float part[2] = {0.f, 0.f};
     if ((int)threadIdx.x < ch.count) {
         const int64_t v = ch.begin + threadIdx.x;
+        const float inv = __ldg(lt.qs + 1);
         float yv[LP], sv[LP], bv[LP];
 #pragma unroll
         for (int g = 0; g < LP / 4; ++g) {
             float4 a = ld4(lt.Ylat, v * (LP / 4) + g);
-            float4 b = ld4(lt.Slat, v * (LP / 4) + g);
+            float4 b = ld4q(lt.Sq, v * (LP / 4) + g, inv);
             float4 c = ld4((const T *)lt.BS, v * (LP / 4) + g);
             yv[4 * g] = a.x; yv[4 * g + 1] = a.y; yv[4 * g + 2] = a.z; yv[4 * g + 3] = a.w;
             sv[4 * g] = b.x; sv[4 * g + 1] = b.y; sv[4 * g + 2] = b.z; sv[4 * g + 3] = b.w;
@@ -464,20 +477,57 @@ __global__ void __launch_bounds__(1024) k_fw_alpha(PartSums P, double *alpha, dc
     }
 }
 
-// Ylat += alpha (Slat - Ylat); BY += alpha (BS - BY) (and its half copy); Slat = 0.
+// Ylat += alpha (Slat - Ylat); BY += alpha (BS - BY) (and its half copy); Sq = 0.
 template <typename T>
 __global__ void k_fw_latupd(FwLat lt, int G, const double *alpha) {
     int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= lt.m * G) return;
     const int64_t v = idx / G;
     const float al = (float)alpha[lt.vimg[v]];
-    float4 y = ld4(lt.Ylat, idx), s = ld4(lt.Slat, idx), by = ld4(lt.BY, idx), bs = ld4((const T *)lt.BS, idx);
+    const float inv = __ldg(lt.qs + 1);
+    float4 y = ld4(lt.Ylat, idx), s = ld4q(lt.Sq, idx, inv), by = ld4(lt.BY, idx), bs = ld4((const T *)lt.BS, idx);
     y.x += al * (s.x - y.x); y.y += al * (s.y - y.y); y.z += al * (s.z - y.z); y.w += al * (s.w - y.w);
     by.x += al * (bs.x - by.x); by.y += al * (bs.y - by.y); by.z += al * (bs.z - by.z); by.w += al * (bs.w - by.w);
     st4(lt.Ylat, idx, y);
     st4(lt.BY, idx, by);
     if (lt.BYh) st4h(lt.BYh, idx, by);
-    st4(lt.Slat, idx, make_float4(0.f, 0.f, 0.f, 0.f));
+    reinterpret_cast<uint4 *>(lt.Sq)[idx] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// Decision trace: row *counter of trace (when below rows) receives s, the
+// conditional gradient the last pixel pass chose (row t = s^t of iteration t).
+__global__ void k_fw_trace(const uint8_t *__restrict__ s, uint8_t *__restrict__ trace, const int *counter, int64_t n,
+                           int rows) {
+    const int t = *counter;
+    if (t >= rows) return;
+    uint8_t *dst = trace + (int64_t)t * n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = s[i];
+}
+
+// Fixed point of the one-hot splat.  An entry of S s is a sum of barycentric
+// weights of the corners at that vertex, at most (S 1)_v; k_fw_s1 forms S 1
+// (float atomics: only a bound is needed), k_fw_qmax its maximum, and
+// k_fw_qscale the largest 2^k <= 2^30 with 2^k (1.001 max (S 1) + 1) <= 2^31,
+// so that the integer sums of the rounded weights cannot overflow.
+__global__ void k_fw_s1(const int32_t *__restrict__ pvid, const float *__restrict__ pbary, int64_t cnt, float *acc) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    const int v = pvid[i];
+    if (v >= 0) atomicAdd(acc + v, pbary[i]);
+}
+__global__ void k_fw_qmax(const float *__restrict__ acc, int64_t m, unsigned *qmax) {
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const float x = v < m ? fmaxf(acc[v], 0.f) : 0.f;
+    const unsigned u = __reduce_max_sync(0xffffffffu, __float_as_uint(x));   // non-negative floats order as integers
+    if ((threadIdx.x & 31) == 0) atomicMax(qmax, u);
+}
+__global__ void k_fw_qscale(const unsigned *qmax, float *qs) {
+    const float b = 1.001f * __uint_as_float(*qmax) + 1.f;
+    int k = 30;
+    while (k > 0 && ldexpf(b, k) > 2147483648.f) --k;
+    qs[0] = ldexpf(1.f, k);
+    qs[1] = ldexpf(1.f, -k);
 }
 
 __global__ void k_fw_to_half(const float *__restrict__ src, __half *__restrict__ dst, int64_t count4) {
@@ -543,6 +593,8 @@ struct Solver {
     int *counter = nullptr, *ticket = nullptr;
     dcrf_fw_record *rec = nullptr;
     int *status = nullptr;
+    uint8_t *trace = nullptr;                  // [trace_rows][n] decisions s^t, or null
+    int trace_rows = 0;
 
     explicit Solver(cudaStream_t st) : s(st), sc(st) {}
 
@@ -599,7 +651,7 @@ struct Solver {
             const size_t cnt = (size_t)(lat->m > 0 ? lat->m : 1) * Lp;
             DCRF_CHECK_STATUS(sc.get(&l.Ylat, cnt));
             DCRF_CHECK_STATUS(sc.get(&l.BY, cnt));
-            DCRF_CHECK_STATUS(sc.get(&l.Slat, cnt));
+            DCRF_CHECK_STATUS(sc.get(&l.Sq, cnt));
             l.BYh = nullptr;
             if (storage == DCRF_STORAGE_F16) DCRF_CHECK_STATUS(sc.get(&l.BYh, cnt));
             char *bs, *tmp;
@@ -668,14 +720,39 @@ struct Solver {
             k_fw_lin<<<nblocks(n * L, 256), 256, 0, s>>>(n, L, unaries, c, musum, nullptr, 1.f, lin, status);
             DCRF_LAUNCHED();
         }
+        // fixed-point scales of the one-hot splats (the blur scratch tmp,
+        // at least m floats, holds S 1)
+        float *qs_all;
+        unsigned *qmax_all;
+        DCRF_CHECK_STATUS(sc.get(&qs_all, (size_t)2 * nk));
+        DCRF_CHECK_STATUS(sc.get(&qmax_all, (size_t)nk));
+        DCRF_TRY(cudaMemsetAsync(qmax_all, 0, nk * sizeof(unsigned), s));
+        for (int m = 0; m < nk; ++m) {
+            FwLat &l = F.l[m];
+            l.qs = qs_all + 2 * m;
+            float *acc = reinterpret_cast<float *>(l.tmp);
+            if (l.m > 0) {
+                DCRF_TRY(cudaMemsetAsync(acc, 0, l.m * sizeof(float), s));
+                const int64_t cnt = n * l.d1;
+                if (cnt > 0) {
+                    k_fw_s1<<<nblocks(cnt, 256), 256, 0, s>>>(l.pvid, l.pbary, cnt, acc);
+                    DCRF_LAUNCHED();
+                }
+                k_fw_qmax<<<nblocks(l.m, 256), 256, 0, s>>>(acc, l.m, qmax_all + m);
+                DCRF_LAUNCHED();
+            }
+            k_fw_qscale<<<1, 1, 0, s>>>(qmax_all + m, qs_all + 2 * m);
+            DCRF_LAUNCHED();
+        }
         // Ylat = S y0, BY = B S y0
         for (int m = 0; m < nk; ++m) {
             FwLat &l = F.l[m];
             DCRF_CHECK_STATUS(dcrf_splat_dense(lattices[m], Y, L, l.Ylat, Lp, s));
             // the splat buffer serves as float32 blur scratch, then is cleared
-            DCRF_CHECK_STATUS(dcrf_blur(lattices[m], l.Ylat, l.BY, l.Slat, Lp, DCRF_STORAGE_F32, false, s));
+            DCRF_CHECK_STATUS(dcrf_blur(lattices[m], l.Ylat, l.BY, reinterpret_cast<float *>(l.Sq), Lp,
+                                        DCRF_STORAGE_F32, false, s));
             const size_t cnt = (size_t)(l.m > 0 ? l.m : 1) * Lp;
-            DCRF_TRY(cudaMemsetAsync(l.Slat, 0, cnt * sizeof(float), s));
+            DCRF_TRY(cudaMemsetAsync(l.Sq, 0, cnt * sizeof(uint32_t), s));
             if (l.BYh && l.m > 0) {
                 k_fw_to_half<<<nblocks(l.m * Lp / 4, 256), 256, 0, s>>>(l.BY, l.BYh, l.m * Lp / 4);
                 DCRF_LAUNCHED();
@@ -821,7 +898,7 @@ struct Solver {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         for (int m = 0; m < nk; ++m)
-            DCRF_TRY(cudaMemsetAsync(F.l[m].Slat, 0, (size_t)(F.l[m].m > 0 ? F.l[m].m : 1) * Lp * sizeof(float), s));
+            DCRF_TRY(cudaMemsetAsync(F.l[m].Sq, 0, (size_t)(F.l[m].m > 0 ? F.l[m].m : 1) * Lp * sizeof(uint32_t), s));
         variant = arg;
         std::lock_guard<std::mutex> lk(mu_);
         cache[key] = arg;
@@ -842,12 +919,19 @@ struct Solver {
     }
 
     dcrf_status pixel(float *Y, const float *phi, bool start) {
+        dcrf_status st;
         if (storage == DCRF_STORAGE_F16)
-            return potts ? pixel_lp<__half, true>(Y, phi, start) : pixel_lp<__half, false>(Y, phi, start);
-        return potts ? pixel_lp<float, true>(Y, phi, start) : pixel_lp<float, false>(Y, phi, start);
+            st = potts ? pixel_lp<__half, true>(Y, phi, start) : pixel_lp<__half, false>(Y, phi, start);
+        else
+            st = potts ? pixel_lp<float, true>(Y, phi, start) : pixel_lp<float, false>(Y, phi, start);
+        if (st != DCRF_OK || !trace || n == 0) return st;
+        k_fw_trace<<<(unsigned)std::min<int64_t>(nblocks(n, 256), 4096), 256, 0, s>>>(sidx, trace, counter, n,
+                                                                                      trace_rows);
+        DCRF_LAUNCHED();
+        return DCRF_OK;
     }
 
-    // d+1 Jacobi passes of Slat into BS for every lattice, one launch per pass
+    // d+1 Jacobi passes of S s (Sq) into BS for every lattice, one launch per pass
     // (tune_only: pick the blur kernel, as run() does before graph capture).
     template <int LPc, typename T>
     dcrf_status blur_t(bool tune_only = false) {
@@ -862,7 +946,8 @@ struct Solver {
         for (int k = 0; k < nk; ++k) {
             const int m = order[k];
             B.l[k].nbr = lats[m]->nbr;
-            B.l[k].src0 = F.l[m].Slat;
+            B.l[k].src0 = F.l[m].Sq;
+            B.l[k].qs = F.l[m].qs;
             B.l[k].dst = F.l[m].BS;
             B.l[k].tmp = F.l[m].tmp;
             B.l[k].m = F.l[m].m;
@@ -915,7 +1000,7 @@ struct Solver {
 
     // Blur tuner: a vertex row per thread (0), label-split rows (1) or the
     // persistent form with the neighbour pair loaded a row ahead (2), timed on
-    // this problem's lattices (the blur only reads Slat and writes BS and tmp,
+    // this problem's lattices (the blur only reads Sq and writes BS and tmp,
     // which every iteration overwrites) and cached per (Lp, storage, size bucket).
     template <int LPc, typename T>
     dcrf_status tune_blur(const BlurSet &B, int dmax) {
@@ -1004,7 +1089,7 @@ struct Solver {
         return potts ? latdot_lp<float, true>(which) : latdot_lp<float, false>(which);
     }
 
-    // One Frank-Wolfe iteration, state at (y, s, Slat = S s, BY = B S y).
+    // One Frank-Wolfe iteration, state at (y, s, Sq = S s, BY = B S y).
     dcrf_status iterate(float *Y, const float *phi) {
         DCRF_CHECK_STATUS(blur_all());
         for (int m = 0; m < nk; ++m) DCRF_CHECK_STATUS(latdot(m));
@@ -1061,14 +1146,17 @@ struct Solver {
 
 }  // namespace
 
-extern "C" dcrf_status dcrf_qp_fw(const float *unaries, const dcrf_lattice *lattices, const float *weights,
-                                  int n_kernels, const float *compat, int L, int iters, float *Y,
-                                  dcrf_fw_record *records, int storage, dcrf_stream stream) {
+extern "C" dcrf_status dcrf_qp_fw_trace(const float *unaries, const dcrf_lattice *lattices, const float *weights,
+                                        int n_kernels, const float *compat, int L, int iters, float *Y,
+                                        dcrf_fw_record *records, uint8_t *s_trace, int storage,
+                                        dcrf_stream stream) {
     if (iters < 0) return DCRF_E_INVAL;
     cudaStream_t s = (cudaStream_t)stream;
     Solver S(s);
     DCRF_CHECK_STATUS(S.setup(unaries, lattices, weights, n_kernels, compat, L, storage, Y, iters));
     if (S.n == 0) return DCRF_OK;
+    S.trace = s_trace;
+    S.trace_rows = iters;
     DCRF_CHECK_STATUS(S.pixel(Y, nullptr, true));
     DCRF_CHECK_STATUS(S.run(Y, iters, nullptr));
     if (records && iters > 0) {
@@ -1080,6 +1168,13 @@ extern "C" dcrf_status dcrf_qp_fw(const float *unaries, const dcrf_lattice *latt
         if (h != 0) return (dcrf_status)h;
     }
     return DCRF_OK;
+}
+
+extern "C" dcrf_status dcrf_qp_fw(const float *unaries, const dcrf_lattice *lattices, const float *weights,
+                                  int n_kernels, const float *compat, int L, int iters, float *Y,
+                                  dcrf_fw_record *records, int storage, dcrf_stream stream) {
+    return dcrf_qp_fw_trace(unaries, lattices, weights, n_kernels, compat, L, iters, Y, records, nullptr, storage,
+                            stream);
 }
 
 extern "C" dcrf_status dcrf_dc_cccp(const float *unaries, const dcrf_lattice *lattices, const float *weights,
@@ -1103,8 +1198,8 @@ extern "C" dcrf_status dcrf_dc_cccp(const float *unaries, const dcrf_lattice *la
         k_fw_lin<<<nblocks(S.n * L, 256), 256, 0, s>>>(S.n, L, unaries, S.c, S.musum, Y, 2.f, S.lin, S.status);
         DCRF_LAUNCHED();
         for (int m = 0; m < S.nk; ++m)
-            DCRF_TRY(cudaMemsetAsync(S.F.l[m].Slat, 0,
-                                     (size_t)(S.F.l[m].m > 0 ? S.F.l[m].m : 1) * S.Lp * sizeof(float), s));
+            DCRF_TRY(cudaMemsetAsync(S.F.l[m].Sq, 0,
+                                     (size_t)(S.F.l[m].m > 0 ? S.F.l[m].m : 1) * S.Lp * sizeof(uint32_t), s));
         DCRF_CHECK_STATUS(S.pixel(Y, inner == 0 ? unaries : nullptr, true));
         DCRF_CHECK_STATUS(S.run(Y, inner, unaries));
         k_fw_qp_energy<<<S.batch, 1024, 0, s>>>(S.parts(), qe + (int64_t)(o + 1) * S.batch);
@@ -1885,7 +1980,7 @@ dcrf_status dense_filter(const dcrf_lattice lat, const float *in, int L, int Lp,
 extern "C" dcrf_status dcrf_qp_fw_backward(const float *unaries, const dcrf_lattice *lattices, const float *weights,
                                            int n_kernels, const float *compat, int L, int iters, const float *Y0,
                                            const float *dYT, float *dphi, float *dY0, double *dweights,
-                                           dcrf_stream stream) {
+                                           uint8_t *s_tape, dcrf_stream stream) {
     if (iters < 0 || !Y0 || !dYT || !dphi) return DCRF_E_INVAL;
     cudaStream_t s = (cudaStream_t)stream;
     Solver S(s);
@@ -1990,6 +2085,8 @@ extern "C" dcrf_status dcrf_qp_fw_backward(const float *unaries, const dcrf_latt
         DCRF_CHECK_STATUS(bw_dispatch(B, Lp, S.potts, nch, false, s));
     }
     if (dY0) DCRF_TRY(cudaMemcpyAsync(dY0, ybar, nl * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    if (s_tape && iters > 0)
+        DCRF_TRY(cudaMemcpyAsync(s_tape, stape, (size_t)iters * n, cudaMemcpyDeviceToDevice, s));
     if (dweights) {
         DCRF_TRY(cudaMemcpyAsync(dweights, wbar, nk * sizeof(double), cudaMemcpyDeviceToHost, s));
         int h = 0;

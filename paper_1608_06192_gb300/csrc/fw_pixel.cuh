@@ -47,7 +47,8 @@ struct FwLat {
     float *Ylat;     // [m][Lp] S y
     float *BY;       // [m][Lp] B S y (float32 master)
     __half *BYh;     // [m][Lp] half copy of BY sliced by the pixel kernel (half storage only)
-    float *Slat;     // [m][Lp] S s
+    uint32_t *Sq;    // [m][Lp] S s in fixed point: value = Sq * qs[1] (integer sums: deterministic)
+    const float *qs; // {2^k, 2^-k} of this lattice's fixed point
     void *BS;        // [m][Lp] B S s (float or half)
     void *tmp;       // blur scratch (same type as BS)
 };
@@ -63,6 +64,10 @@ __device__ __forceinline__ float4 ld4(const __half *p, int64_t i) {
     float2 a = __half22float2(*reinterpret_cast<__half2 *>(&raw.x));
     float2 b = __half22float2(*reinterpret_cast<__half2 *>(&raw.y));
     return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float4 ld4q(const uint32_t *p, int64_t i, float inv) {
+    const uint4 u = reinterpret_cast<const uint4 *>(p)[i];
+    return make_float4((float)u.x * inv, (float)u.y * inv, (float)u.z * inv, (float)u.w * inv);
 }
 __device__ __forceinline__ void st4(float *p, int64_t i, float4 v) { reinterpret_cast<float4 *>(p)[i] = v; }
 __device__ __forceinline__ void st4h(__half *p, int64_t i, float4 v) {
@@ -108,7 +113,9 @@ __device__ __forceinline__ void block_reduce_add(double (&v)[N], double *acc) {
 //   4: -sum_w <y', mu e_s'> + y'(s') d(s')   (pixel part of <y', (Psi+D) s'>)
 //   5: -sum_w mu(s', s') + d(s')            (pixel part of <s', (Psi+D) s'>)
 //   6: <y', D y'>  7: <phi, y'> (only when phi is given)
-// and S s' is splatted into Slat.
+// and S s' is splatted into Sq: every corner adds its barycentric weight
+// rounded to a multiple of 2^-k (integer reductions in L2, so the sums and
+// everything after them do not depend on the order of the atomics).
 struct PixArgs {
     const Chunk *chunks;
     const double *alpha;   // [batch] or null (start: alpha = 0)
@@ -532,16 +539,17 @@ __device__ __forceinline__ void pixel_chunk(const PixArgs &A, const FwLats &F, c
         }
       }
         A.s[a] = (uint8_t)sb;
-        // splat of the one-hot s' into Slat (FP32 reductions in L2).  A delta
+        // splat of the one-hot s' into Sq (integer reductions in L2).  A delta
         // update (+b at s', -b at s) does not pay: along the Frank-Wolfe path
         // almost every pixel's argmin moves at every iteration.
 #pragma unroll
         for (int mm = 0; mm < DCRF_MAX_KERNELS; ++mm) {
             if (mm >= F.nk) break;
             const FwLat &lt = F.l[mm];
+            const float q = __ldg(lt.qs);
             for (int k = 0; k < lt.d1; ++k) {
                 const int v = __ldg(lt.pvid + a * lt.d1 + k);
-                if (v >= 0) atomicAdd(lt.Slat + (int64_t)v * LP + sb, __ldg(lt.pbary + a * lt.d1 + k));
+                if (v >= 0) atomicAdd(lt.Sq + (int64_t)v * LP + sb, __float2uint_rn(q * __ldg(lt.pbary + a * lt.d1 + k)));
             }
         }
     }
@@ -701,9 +709,11 @@ __device__ __forceinline__ void pixel3(const PixArgs &A, const FwLats &F, const 
         for (int mm = 0; mm < DCRF_MAX_KERNELS; ++mm) {
             if (mm >= F.nk) break;
             const FwLat &lt = F.l[mm];
+            const float qk = __ldg(lt.qs);
             for (int k = q; k < lt.d1; k += 3) {
                 const int v = __ldg(lt.pvid + a * lt.d1 + k);
-                if (v >= 0) atomicAdd(lt.Slat + (int64_t)v * LP + sbw, __ldg(lt.pbary + a * lt.d1 + k));
+                if (v >= 0)
+                    atomicAdd(lt.Sq + (int64_t)v * LP + sbw, __float2uint_rn(qk * __ldg(lt.pbary + a * lt.d1 + k)));
             }
         }
     }

@@ -91,24 +91,68 @@ def test_backward_matches_oracle_and_finite_differences(dcrf):
     assert checked >= 6
 
 
-def test_backward_21_labels_against_oracle(dcrf):
-    # With 21 labels some argmin decisions of the FP64 path sit within FP32
-    # rounding of a tie, so a few of them can go the other way on the GPU and
-    # perturb every step size slightly: the weight gradient and the direction
-    # of the unary gradient are compared.
+def test_backward_21_labels_along_the_gpu_path(dcrf):
+    # With 21 labels some argmin decisions of the path sit within FP32
+    # rounding of a tie, so FP32 and FP64 runs may take different smooth
+    # pieces of the unrolled map.  The GPU returns the decisions s^t of the
+    # forward it differentiated; the oracle replays them (each must be an
+    # argmin of the FP64 gradient up to the FP32 filter tolerance) and both
+    # sides then differentiate the same piece: 1e-4 against the oracle's
+    # reverse mode and against FP64 central differences (h = 1e-4) along it.
+    iters = 10
     p = S.crop(S.make_problem(48, 40, 5, 21, seed=3), 32, 24)
     ybar = np.random.default_rng(1).normal(size=(p.n_pixels, p.n_labels))
-    _, dphi, dw = _gpu_grad(dcrf, [p], ybar, 10)
+    g = gpu_setup(dcrf, [p], torch)
+    dYT = torch.from_numpy(ybar.astype(np.float32)).cuda()
+    dphi, dw, _, st = dcrf.dcrf_qp_fw_backward(g["phi"], [g["lb"], g["ls"]], p.weights, g["y0"], dYT, iters,
+                                               tape=True)
+    dphi, dec = dphi.cpu().numpy(), st.cpu().numpy().astype(np.int64)
     c = _oracle(p)
-    _, tape = qp.fw_tape(c, p.y0, 10)
+    _, tape = qp.fw_tape(c, p.y0, iters, decisions=dec)
+    bound = 4 * 1e-4 * float(sum(w * o for w, o in zip(c.w, c.o)).max())
+    rows = np.arange(c.n)
+    for t, (y, _, _, _, _) in enumerate(tape):
+        gr = c.phi - c.d + 2.0 * c.op(y)
+        assert float((gr[rows, dec[t]] - gr.min(axis=1)).max()) <= bound
     phibar, wbar, _ = qp.fw_backward(c, tape, ybar)
-    np.testing.assert_allclose(dw, wbar, rtol=1e-3)
-    cos = float(np.sum(dphi * phibar) / np.linalg.norm(dphi) / np.linalg.norm(phibar))
-    assert cos >= 0.99
+    assert rel_err(dphi, phibar) <= 1e-4
+    assert rel_err(dw, wbar) <= 1e-4
+    h = 1e-4
+
+    def loss(w=None, phi=None):
+        y, tp = qp.fw_tape(_oracle(p, w, phi), p.y0, iters, decisions=dec)
+        assert all((0 < a[2] < 1) == (0 < b[2] < 1) for a, b in zip(tp, tape))
+        return float(np.sum(ybar * y))
+
+    def central(**kw):
+        fp, fm = loss(**{k: v[0] for k, v in kw.items()}), loss(**{k: v[1] for k, v in kw.items()})
+        return (fp - fm) / (2 * h), 8 * np.finfo(float).eps * max(abs(fp), abs(fm)) / (2 * h)
+
+    for m in range(2):
+        wp = np.array(p.weights, float); wp[m] += h
+        wm = np.array(p.weights, float); wm[m] -= h
+        fd, floor = central(w=(wp, wm))
+        assert abs(dw[m] - fd) <= 1e-4 * abs(fd) + floor
+    rng = np.random.default_rng(4)
+    for _ in range(8):
+        a, i = int(rng.integers(p.n_pixels)), int(rng.integers(p.n_labels))
+        php = p.unaries.astype(np.float64).copy(); php[a, i] += h
+        phm = p.unaries.astype(np.float64).copy(); phm[a, i] -= h
+        fd, floor = central(phi=(php, phm))
+        # the GPU value carries FP32 rounding: 1e-4 of the largest entry
+        assert abs(dphi[a, i] - fd) <= 1e-4 * np.abs(phibar).max() + floor
 
 
-def test_autograd_function_on_batch(dcrf):
+def test_autograd_function_on_batch(dcrf, monkeypatch):
+    # The one-hot splat sums fixed-point weights with integer reductions, so a
+    # run does not depend on the order of the atomics, and an image of a batch
+    # is processed exactly as alone when the same kernel variants run (forced
+    # here: the tuners may choose others for other sizes).  Every image then
+    # gets the gradient it gets alone up to the order of the FP64 reductions
+    # of the reverse sweep, and the weight gradient is the sum over images.
     from paper_1608_06192_gb300.autograd import FrankWolfeQP
+    monkeypatch.setenv("DCRF_PIXEL_VARIANT", "14")
+    monkeypatch.setenv("DCRF_BLUR_VARIANT", "0")
     probs = [S.make_problem(320, 213, 30, 21, seed=60 + i) for i in range(8)]
     g = gpu_setup(dcrf, probs, torch)
     phi = g["phi"].clone().requires_grad_(True)
@@ -119,16 +163,10 @@ def test_autograd_function_on_batch(dcrf):
     (y * G).sum().backward()
     dphi = phi.grad.cpu().numpy()
     assert np.isfinite(dphi).all() and torch.isfinite(w.grad).all()
-    # every image of the batch gets the gradient it gets alone (up to argmin
-    # ties that FP32 rounding may decide either way: the splat's reductions
-    # run in a different order in the batch, and with 21 labels some argmin
-    # margins are ~1e-7 relative) and the weight gradient is the sum over the
-    # images
     dw_sum = np.zeros(2)
     for b in range(8):
         s0, s1 = g["off"][b], g["off"][b + 1]
         _, dphi_b, dw_b = _gpu_grad(dcrf, [probs[b]], ybar[s0:s1], 10)
         dw_sum += dw_b
-        cos = float(np.sum(dphi[s0:s1] * dphi_b) / np.linalg.norm(dphi[s0:s1]) / np.linalg.norm(dphi_b))
-        assert cos >= 0.99
-    assert rel_err(w.grad.numpy(), dw_sum) <= 3e-3
+        assert rel_err(dphi[s0:s1], dphi_b) <= 1e-5
+    assert rel_err(w.grad.numpy(), dw_sum) <= 1e-5

@@ -69,3 +69,45 @@ def test_gradients_match_central_differences():
         assert abs(fd - phibar[a, i]) <= 1e-4 * max(abs(fd), 1e-6) + 1e-9, (a, i, fd, phibar[a, i])
         checked += 1
     assert checked >= 8
+
+
+def test_gradients_along_given_decisions_match_central_differences_21_labels():
+    # With 21 labels the FP64 path has argmin decisions within ~1e-7 of a tie,
+    # so perturbing phi or w by h = 1e-4 changes s^t and plain differences
+    # jump.  With the decisions held fixed (the smooth piece of the unrolled
+    # map, the replay mode of the forward), central differences are the
+    # derivative that the reverse mode computes.
+    p = S.crop(S.make_problem(48, 40, 5, 21, seed=3), 32, 24)
+    iters = 10
+    ybar = np.random.default_rng(1).normal(size=(p.n_pixels, p.n_labels))
+    c = _crf(p)
+    y, tape = qp.fw_tape(c, p.y0, iters)
+    dec = [np.argmax(t[1], axis=1) for t in tape]
+    phibar, wbar, _ = qp.fw_backward(c, tape, ybar)
+    # the replay of the run's own decisions is the run itself
+    y_r, tape_r = qp.fw_tape(c, p.y0, iters, decisions=dec)
+    np.testing.assert_array_equal(y, y_r)
+    h = 1e-4
+
+    def loss(w=None, phi=None):
+        yy, tp = qp.fw_tape(_crf(p, w, phi), p.y0, iters, decisions=dec)
+        assert all((0 < a[2] < 1) == (0 < b[2] < 1) for a, b in zip(tp, tape))
+        return float(np.sum(ybar * yy))
+
+    def central(**kw):
+        """(difference quotient, its FP64 rounding floor 8 eps |f| / 2h)."""
+        fp, fm = loss(**{k: v[0] for k, v in kw.items()}), loss(**{k: v[1] for k, v in kw.items()})
+        return (fp - fm) / (2 * h), 8 * np.finfo(float).eps * max(abs(fp), abs(fm)) / (2 * h)
+
+    for m in range(2):
+        wp = np.array(p.weights, dtype=np.float64); wp[m] += h
+        wm = np.array(p.weights, dtype=np.float64); wm[m] -= h
+        fd, floor = central(w=(wp, wm))
+        assert abs(fd - wbar[m]) <= 1e-4 * abs(fd) + floor, (m, fd, wbar[m])
+    rng = np.random.default_rng(2)
+    for _ in range(8):
+        a, i = int(rng.integers(p.n_pixels)), int(rng.integers(p.n_labels))
+        php = p.unaries.astype(np.float64).copy(); php[a, i] += h
+        phm = p.unaries.astype(np.float64).copy(); phm[a, i] -= h
+        fd, floor = central(phi=(php, phm))
+        assert abs(fd - phibar[a, i]) <= 1e-4 * abs(fd) + floor, (a, i, fd, phibar[a, i], floor)

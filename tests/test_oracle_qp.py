@@ -99,3 +99,38 @@ def test_cccp_monotone(kind):
     y, e = qp.cccp_dc_gen(c, y0, outer=6, inner=15)
     assert np.all(np.diff(e) <= 1e-9 * np.abs(e).max())
     np.testing.assert_allclose(e[-1], c.s_qp(y), rtol=1e-9)
+
+
+def test_replayed_decisions_follow_the_definitions():
+    # Replaying decisions (another run's s^t) must reproduce the free run when
+    # they are the run's own argmins, and otherwise follow Algorithm 1 and
+    # Appendix B along the given vertices: energy S_cvx(y^t) (Eq. 10), gap
+    # <g, y^t - s^t>, A and B the coefficients of S_cvx(y^t + a (s^t - y^t)),
+    # y^{t+1} = y^t + alpha (s^t - y^t).
+    c, y0 = _brute_problem(5, n=18, L=4)
+    own = []
+    y1, _, rec1 = qp.frank_wolfe(c, y0, 7, on_step=lambda t, g, s: own.append(np.array(s)))
+    y2, _, rec2 = qp.frank_wolfe(c, y0, 7, decisions=own)
+    np.testing.assert_array_equal(y1, y2)
+    np.testing.assert_array_equal(rec1, rec2)
+    assert all(np.array_equal(s, np.argmin(c.phi - c.d + 2 * c.psi_plus_D(y), 1)) for s, y in
+               zip(own[:1], [y0]))
+    rng = np.random.default_rng(3)
+    dec = rng.integers(0, c.L, size=(7, c.n))
+    grads = []
+    y3, _, rec3 = qp.frank_wolfe(c, y0, 7, decisions=dec, on_step=lambda t, g, s: grads.append(g.copy()))
+    y = np.array(y0, dtype=np.float64)
+    rows = np.arange(c.n)
+    for t in range(7):
+        s = np.zeros_like(y)
+        s[rows, dec[t]] = 1.0
+        np.testing.assert_allclose(rec3[t, 0], c.s_cvx(y), rtol=1e-12)
+        g = c.phi - c.d + 2 * c.psi_plus_D(y)
+        np.testing.assert_allclose(grads[t], g, rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(rec3[t, 1], np.sum(g * (y - s)), rtol=1e-10, atol=1e-10)
+        for a in (0.25, 0.8):
+            pred = c.s_cvx(y) + rec3[t, 4] * a + rec3[t, 3] * a * a
+            np.testing.assert_allclose(c.s_cvx(y + a * (s - y)), pred, rtol=1e-11)
+        assert rec3[t, 2] == qp.step_size(rec3[t, 3], rec3[t, 4])
+        y = y + rec3[t, 2] * (s - y)
+    np.testing.assert_allclose(y3, y, rtol=1e-12, atol=1e-14)
