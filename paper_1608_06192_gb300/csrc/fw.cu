@@ -530,6 +530,54 @@ __global__ void k_fw_qscale(const unsigned *qmax, float *qs) {
     qs[1] = ldexpf(1.f, -k);
 }
 
+// y^0 must lie on the simplex (rows non-negative, summing to one within
+// 1e-5); a row that does not is reported as DCRF_E_INVAL.
+__global__ void k_fw_check_y(const float *__restrict__ Y, int64_t n, int L, int *status) {
+    const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    float sum = 0.f;
+    bool ok = true;
+    for (int i = 0; i < L; ++i) {
+        const float y = Y[a * L + i];
+        ok = ok && y >= 0.f;
+        sum += y;
+    }
+    if (!ok || !(fabsf(sum - 1.f) <= 1e-5f)) dcrf_flag(status, DCRF_E_INVAL);
+}
+
+// S y^0 in the fixed point of the one-hot splat, so that the solver's state
+// does not depend on the order of atomics either: one thread per (point,
+// pair of labels) adds round(2^k w y) of both labels of the pair with one
+// 64-bit integer reduction (low and high word; a word's sum stays below 2^32,
+// since 0 <= y <= 1 bounds it by 2^k (S 1)_v + the roundings, so no carry
+// crosses into the other label).
+__global__ void k_fw_splat_y0(const float *__restrict__ Y, int64_t n, int L, int Lp, int D1,
+                              const int32_t *__restrict__ pvid, const float *__restrict__ pbary, const float *qs,
+                              uint32_t *Sq) {
+    const int H = Lp >> 1;
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * H) return;
+    const int64_t a = idx / H;
+    const int c0 = 2 * (int)(idx - a * H);
+    const float q = __ldg(qs);
+    const float y0 = c0 < L ? fmaxf(Y[a * L + c0], 0.f) : 0.f;
+    const float y1 = c0 + 1 < L ? fmaxf(Y[a * L + c0 + 1], 0.f) : 0.f;
+    for (int k = 0; k < D1; ++k) {
+        const int v = pvid[a * D1 + k];
+        if (v < 0) continue;
+        const float w = q * pbary[a * D1 + k];
+        const unsigned long long lo = __float2uint_rn(w * y0), hi = __float2uint_rn(w * y1);
+        if (lo | hi)
+            atomicAdd(reinterpret_cast<unsigned long long *>(Sq + (int64_t)v * Lp + c0), lo | (hi << 32));
+    }
+}
+
+// V = Sq 2^-k as float32.
+__global__ void k_fw_dequant(const uint32_t *__restrict__ Sq, int64_t count4, const float *qs, float *V) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < count4) st4(V, i, ld4q(Sq, i, __ldg(qs + 1)));
+}
+
 __global__ void k_fw_to_half(const float *__restrict__ src, __half *__restrict__ dst, int64_t count4) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < count4) st4h(dst, i, ld4(src, i));
@@ -744,14 +792,26 @@ struct Solver {
             k_fw_qscale<<<1, 1, 0, s>>>(qmax_all + m, qs_all + 2 * m);
             DCRF_LAUNCHED();
         }
-        // Ylat = S y0, BY = B S y0
+        // Ylat = S y0 (fixed point, then float32), BY = B S y0
+        if (n > 0) {
+            k_fw_check_y<<<nblocks(n, 256), 256, 0, s>>>(Y, n, L, status);
+            DCRF_LAUNCHED();
+        }
         for (int m = 0; m < nk; ++m) {
             FwLat &l = F.l[m];
-            DCRF_CHECK_STATUS(dcrf_splat_dense(lattices[m], Y, L, l.Ylat, Lp, s));
+            const size_t cnt = (size_t)(l.m > 0 ? l.m : 1) * Lp;
+            DCRF_TRY(cudaMemsetAsync(l.Sq, 0, cnt * sizeof(uint32_t), s));
+            if (n > 0 && l.m > 0) {
+                ProfScope ps(P_SPLAT_DENSE, s);
+                k_fw_splat_y0<<<nblocks(n * (Lp / 2), 256), 256, 0, s>>>(Y, n, L, Lp, l.d1, l.pvid, l.pbary, l.qs,
+                                                                         l.Sq);
+                DCRF_LAUNCHED();
+                k_fw_dequant<<<nblocks(l.m * Lp / 4, 256), 256, 0, s>>>(l.Sq, l.m * Lp / 4, l.qs, l.Ylat);
+                DCRF_LAUNCHED();
+            }
             // the splat buffer serves as float32 blur scratch, then is cleared
             DCRF_CHECK_STATUS(dcrf_blur(lattices[m], l.Ylat, l.BY, reinterpret_cast<float *>(l.Sq), Lp,
                                         DCRF_STORAGE_F32, false, s));
-            const size_t cnt = (size_t)(l.m > 0 ? l.m : 1) * Lp;
             DCRF_TRY(cudaMemsetAsync(l.Sq, 0, cnt * sizeof(uint32_t), s));
             if (l.BYh && l.m > 0) {
                 k_fw_to_half<<<nblocks(l.m * Lp / 4, 256), 256, 0, s>>>(l.BY, l.BYh, l.m * Lp / 4);

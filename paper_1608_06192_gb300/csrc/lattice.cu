@@ -450,6 +450,20 @@ dcrf_status dcrf_blur(const dcrf_lattice lat, const float *src, void *dst, void 
     return blur_typed<float>(lat, src, (float *)dst, (float *)tmp, Lp, reverse, s);
 }
 
+// S 1 in fixed point: acc[v] += round(2^32 w) over the corners at v (w <= 1,
+// so a sum stays far below 2^64); k_ones_rows writes the rows (S 1, 0, 0, 0).
+__global__ void k_splat_ones_q(const int32_t *__restrict__ pvid, const float *__restrict__ pbary, int64_t cnt,
+                               unsigned long long *acc) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    const int v = pvid[i];
+    if (v >= 0) atomicAdd(acc + v, (unsigned long long)__double2ull_rn(ldexp((double)pbary[i], 32)));
+}
+__global__ void k_ones_rows(const unsigned long long *__restrict__ acc, int64_t m, float *V) {
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v < m) reinterpret_cast<float4 *>(V)[v] = make_float4((float)ldexp((double)acc[v], -32), 0.f, 0.f, 0.f);
+}
+
 // Dense splat: V[vertex_k(a)][c] += b_k(a) * Y[a][c]; one thread per (point,
 // group of four labels), one 16-byte vector reduction per simplex corner.
 __global__ void k_splat_dense(const float *__restrict__ Y, int64_t n, int L, int Lp, int D1,
@@ -725,18 +739,21 @@ static dcrf_status build_typed(dcrf_lattice lat, const float *feat, cudaStream_t
                                                            lat->nbr);
         DCRF_LAUNCHED();
     }
-    // K~ 1 for the d vector of Eq. 11
-    if (n > 0) {
+    // K~ 1 for the d vector of Eq. 11; S 1 is summed in 64-bit fixed point
+    // (integer sums: the same lattice comes out of every build of the same
+    // points, bit for bit)
+    if (n > 0 && m > 0) {
         float *V, *A, *B;
+        unsigned long long *acc;
         DCRF_CHECK_STATUS(sc.get(&V, (size_t)m * 4));
         DCRF_CHECK_STATUS(sc.get(&A, (size_t)m * 4));
         DCRF_CHECK_STATUS(sc.get(&B, (size_t)m * 4));
-        float *ones_in;
-        DCRF_CHECK_STATUS(sc.get(&ones_in, (size_t)n));
-        DCRF_TRY(cudaMemsetAsync(V, 0, (size_t)m * 4 * sizeof(float), s));
-        // fill ones (float 1.0f bit pattern is not bytewise, use a kernel)
-        DCRF_CHECK_STATUS(dcrf_fill(ones_in, 1.0f, n, s));
-        DCRF_CHECK_STATUS(dcrf_splat_dense(lat, ones_in, 1, V, 4, s));
+        DCRF_CHECK_STATUS(sc.get(&acc, (size_t)m));
+        DCRF_TRY(cudaMemsetAsync(acc, 0, (size_t)m * sizeof(unsigned long long), s));
+        k_splat_ones_q<<<blocks_for(n * D1, 256), 256, 0, s>>>(lat->pvid, lat->pbary, n * D1, acc);
+        DCRF_LAUNCHED();
+        k_ones_rows<<<blocks_for(m, 256), 256, 0, s>>>(acc, m, V);
+        DCRF_LAUNCHED();
         DCRF_CHECK_STATUS(dcrf_blur(lat, V, A, B, 4, DCRF_STORAGE_F32, false, s));
         k_slice<float><<<blocks_for(n, 256), 256, 0, s>>>(A, n, 1, 1, D1, lat->pvid, lat->pbary, (float)lat->s0,
                                                           lat->ones);

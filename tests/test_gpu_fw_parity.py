@@ -15,18 +15,11 @@ that bound could not have been chosen by a correct kernel.
 import numpy as np
 import pytest
 
-from helpers import gpu_setup, oracle_crf
-from oracle import qp
+from helpers import check_replay, gpu_setup, replay_image
 from paper_1608_06192_gb300 import synthetic as S
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
-
-TOL_FILTER = {"f32": 1e-4, "f16": 2e-3}   # filter tolerances (relative to the largest entry)
-TOL_ENERGY = 1e-3                          # relaxed energies, relative
-TOL_COEF = 1e-3                            # A, B, gap: relative to the largest |energy| of the image
-TOL_ALPHA = 1e-3                           # step sizes, absolute
-TOL_Y = 1e-3                               # y^T per element, absolute
 
 
 def _run(dcrf, probs, iters, storage):
@@ -34,43 +27,6 @@ def _run(dcrf, probs, iters, storage):
     Y = g["y0"].clone()
     rec, trace = dcrf.dcrf_qp_fw_trace(g["phi"], [g["lb"], g["ls"]], probs[0].weights, Y, iters, storage=storage)
     return g, Y.cpu().numpy(), rec, trace.cpu().numpy()
-
-
-def replay_image(p, y_gpu, rec_gpu, dec, storage, iters):
-    """Replays the GPU's decisions in the oracle; returns the measured errors."""
-    c = oracle_crf(p)
-    bound = 4.0 * TOL_FILTER[storage] * float((c.c_raw + c.kernel.sum_w).max())
-    rows = np.arange(c.n)
-    stat = {"excess": 0.0, "agree": 0, "total": 0}
-
-    def on_step(t, g, s):
-        ex = g[rows, s] - g.min(axis=1)
-        stat["excess"] = max(stat["excess"], float(ex.max()))
-        stat["agree"] += int(np.sum(s == np.argmin(g, axis=1)))
-        stat["total"] += c.n
-
-    y_o, _, rec_o = qp.frank_wolfe(c, p.y0, iters, decisions=dec.astype(np.int64), on_step=on_step)
-    escale = np.abs(rec_o[:, 0]).max()
-    return {
-        "excess_over_bound": stat["excess"] / bound,
-        "agree": stat["agree"] / max(1, stat["total"]),
-        "energy": float(np.abs(rec_gpu[:, 0] - rec_o[:, 0]).max() / escale),
-        "gap": float(np.abs(rec_gpu[:, 1] - rec_o[:, 1]).max() / escale),
-        "alpha": float(np.abs(rec_gpu[:, 2] - rec_o[:, 2]).max()),
-        "A": float(np.abs(rec_gpu[:, 3] - rec_o[:, 3]).max() / escale),
-        "B": float(np.abs(rec_gpu[:, 4] - rec_o[:, 4]).max() / escale),
-        "y": float(np.abs(y_gpu.astype(np.float64) - y_o).max()),
-        "final_energy": abs(c.s_cvx(y_gpu.astype(np.float64)) - c.s_cvx(y_o)) / abs(c.s_cvx(y_o)),
-    }
-
-
-def check(err, where=""):
-    print(f"\n{where}: " + ", ".join(f"{k} {v:.3g}" for k, v in err.items()))
-    assert err["excess_over_bound"] <= 1.0, where
-    assert err["energy"] <= TOL_ENERGY and err["final_energy"] <= TOL_ENERGY, where
-    assert err["gap"] <= TOL_COEF and err["A"] <= TOL_COEF and err["B"] <= TOL_COEF, where
-    assert err["alpha"] <= TOL_ALPHA, where
-    assert err["y"] <= TOL_Y, where
 
 
 def _parity(dcrf, probs, iters, storage, images=None):
@@ -82,7 +38,7 @@ def _parity(dcrf, probs, iters, storage, images=None):
         p = probs[b]
         assert trace[:, s0:s1].max() < p.n_labels
         err = replay_image(p, Y[s0:s1], rec[:, b], trace[:, s0:s1], storage, iters)
-        check(err, f"{storage} image {b} ({p.width}x{p.height}, L={p.n_labels}, {iters} iterations)")
+        check_replay(err, f"{storage} image {b} ({p.width}x{p.height}, L={p.n_labels}, {iters} iterations)")
         out.append(err)
     return g, Y, rec, out
 
