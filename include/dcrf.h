@@ -139,8 +139,10 @@ dcrf_status dcrf_filter(dcrf_lattice lat, const float *Y, int L, float *out, int
  * which every GPU that loads the library holds until the process exits.
  * Requests with lattice vertices * round4(L) * (4 + 2 * value size) bytes
  * (each part rounded up to 256) above that size return DCRF_E_SCRATCH.
- * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  All
+ * The array's device address is looked up once per device (with that device
+ * current) by dcrf_lattice_build, or else by the first dcrf_filter_static
+ * call on the stream's device; when a call has to do it, make that call
+ * before any stream capture.  All
  * calls share the array and it keeps the last call's contents (the splat
  * buffer is cleared on entry): calls that overlap on the GPU race, so
  * serialise them.
@@ -370,6 +372,19 @@ dcrf_status dcrf_pool_trim(void);
 dcrf_status dcrf_profile_enable(int on);
 dcrf_status dcrf_profile_reset(void);
 int dcrf_profile_read(const char **names, int64_t *launches, double *ms, int capacity);
+
+/*
+ * Self-test of the bounded device-side wait (no counterpart in the paper).
+ * The pixel pass of the Frank-Wolfe solver waits for its tile copies on an
+ * mbarrier with a bounded number of polls and flags DCRF_E_TIMEOUT when they
+ * run out instead of hanging.  This launches one block that polls an
+ * mbarrier `polls` times (1 <= polls <= 2^26): with never_complete != 0 the
+ * barrier waits for bytes that nothing sends (no copy is in flight), so the
+ * wait runs out and DCRF_E_TIMEOUT lands in lat's status word (read it with
+ * dcrf_lattice_status); with never_complete == 0 it completes at once.
+ * Asynchronous; the context stays usable either way.
+ */
+dcrf_status dcrf_selftest_bounded_wait(dcrf_lattice lat, int64_t polls, int never_complete, dcrf_stream stream);
 
 /* Euclidean projection of every row of V [N][L] onto the simplex (device). */
 dcrf_status dcrf_simplex_project(const float *V, int64_t n, int L, float *Y, dcrf_stream stream);

@@ -70,6 +70,7 @@ _SIGS = {
     "dcrf_pool_trim": ([], _I),
     "dcrf_round_kt": ([_P, _I64, _I, _I, _P, _P, _I, _P, _P, _P], _I),
     "dcrf_simplex_project": ([_P, _I64, _I, _P, _P], _I),
+    "dcrf_selftest_bounded_wait": ([_P, _I64, _I, _P], _I),
     "dcrf_profile_enable": ([_I], _I),
     "dcrf_profile_reset": ([], _I),
     "dcrf_profile_read": ([_P, _P, _P, _I], _I),
@@ -515,6 +516,12 @@ def dcrf_simplex_project(V: torch.Tensor, stream=None) -> torch.Tensor:
     _check(lib().dcrf_simplex_project(_ptr(V), V.shape[0], V.shape[1], _ptr(Y), _stream(stream)),
            "dcrf_simplex_project")
     return Y
+
+
+def dcrf_selftest_bounded_wait(lat: Lattice, polls: int, never_complete: bool, stream=None):
+    """Launches the bounded-wait self-test; the outcome lands in lat's status word."""
+    _check(lib().dcrf_selftest_bounded_wait(lat.handle, int(polls), 1 if never_complete else 0, _stream(stream)),
+           "dcrf_selftest_bounded_wait")
 
 
 def exported_symbols() -> list[str]:

@@ -147,5 +147,11 @@ dcrf_status dcrf_splat_dense(const dcrf_lattice lat, const float *Y, int L, floa
 // scratch of the same type as dst.  src is left intact.
 dcrf_status dcrf_blur(const dcrf_lattice lat, const float *src, void *dst, void *tmp, int Lp,
                       int storage, bool reverse, cudaStream_t s);
-// out [n][L] = s0 * slice of float32 lattice values V [m][Lp].
+// out [n][L] = s0 * slice of lattice values V [m][Lp] (float32, or float16
+// when storage is DCRF_STORAGE_F16).
+dcrf_status dcrf_slice(const dcrf_lattice lat, const void *V, int Lp, int L, int storage, float *out,
+                       cudaStream_t s);
 dcrf_status dcrf_slice_f32(const dcrf_lattice lat, const float *V, int Lp, int L, float *out, cudaStream_t s);
+// Looks up, once per device, the device address of dcrf_filter_static's
+// array for the device of stream s (noalloc.cu).
+dcrf_status dcrf_static_scratch(cudaStream_t s, unsigned char **out);

@@ -1230,6 +1230,38 @@ extern "C" dcrf_status dcrf_qp_fw_trace(const float *unaries, const dcrf_lattice
     return DCRF_OK;
 }
 
+namespace {
+
+// Test of the bounded mbarrier wait that the pixel pass uses for its tile
+// copies: one block arms an mbarrier and polls it `polls` times.  With
+// never_complete, the barrier expects 16 bytes that no copy delivers (nothing
+// is in flight), so the wait runs out and DCRF_E_TIMEOUT is flagged;
+// otherwise the phase completes at once.  The barrier is invalidated before
+// the block exits.
+__global__ void k_wait_selftest(int *status, long long polls, int never_complete) {
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar);
+        if (never_complete) mbar_expect_tx(&bar, 16u);
+        else mbar_arrive(&bar);
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(&bar, polls);
+    if (__syncthreads_and(ok) == 0 && threadIdx.x == 0) dcrf_flag(status, DCRF_E_TIMEOUT);
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_inval(&bar);
+}
+
+}  // namespace
+
+extern "C" dcrf_status dcrf_selftest_bounded_wait(dcrf_lattice lat, int64_t polls, int never_complete,
+                                                  dcrf_stream stream) {
+    if (!lat || polls < 1 || polls > (1ll << 26)) return DCRF_E_INVAL;
+    k_wait_selftest<<<1, 32, 0, (cudaStream_t)stream>>>(lat->status, (long long)polls, never_complete ? 1 : 0);
+    DCRF_LAUNCHED();
+    return DCRF_OK;
+}
+
 extern "C" dcrf_status dcrf_qp_fw(const float *unaries, const dcrf_lattice *lattices, const float *weights,
                                   int n_kernels, const float *compat, int L, int iters, float *Y,
                                   dcrf_fw_record *records, int storage, dcrf_stream stream) {

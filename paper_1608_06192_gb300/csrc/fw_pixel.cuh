@@ -213,9 +213,17 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
                  ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_inval(unsigned long long *bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+}
+constexpr long long kWaitPolls = 1ll << 22;        // first bounded wait of a tile copy
+constexpr long long kWaitPollsLast = 1ll << 26;    // the second one, after DCRF_E_TIMEOUT was flagged
 // Waits for phase 0 of bar with a bounded number of polls; false on timeout.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar) {
-    for (int i = 0; i < (1 << 22); ++i) {
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, long long polls = kWaitPolls) {
+    for (long long i = 0; i < polls; ++i) {
         unsigned done;
         asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
                      " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(smem_addr(bar)) : "memory");
@@ -344,8 +352,12 @@ __device__ __forceinline__ void gather_pair(const FwLat &la, const FwLat &lb, in
 }
 
 // One chunk: every pixel of it (see the comment above PixArgs).
+// Returns false (for the whole block) when the chunk's tile copy did not
+// complete within both bounded waits: DCRF_E_TIMEOUT is then flagged, the
+// block touches neither the tile nor y, s and the splat, and the launch's
+// outputs are invalid.
 template <int LP, typename TB, bool POTTS, int MODE>
-__device__ __forceinline__ void pixel_chunk(const PixArgs &A, const FwLats &F, const Chunk &ch, float *sy,
+__device__ __forceinline__ bool pixel_chunk(const PixArgs &A, const FwLats &F, const Chunk &ch, float *sy,
                                             const float *sl, float (&part)[NS], unsigned long long *tbar) {
     const int L = A.L;
     const bool start = A.alpha == nullptr;
@@ -386,18 +398,24 @@ __device__ __forceinline__ void pixel_chunk(const PixArgs &A, const FwLats &F, c
             }
         }
     }
+    bool tile_ok = true;
     if constexpr ((MODE & kEarly) != 0) {
         // the tile copies were left in flight during the gather
         if (tbar) {
             if (!mbar_wait(tbar)) {
-                // report, then wait (bounded) for the copies still in flight
+                // report, then wait (bounded, longer) for the copies still in flight
                 dcrf_flag(A.status, DCRF_E_TIMEOUT);
-                mbar_wait(tbar);
+                tile_ok = mbar_wait(tbar, kWaitPollsLast);
             }
         } else {
             cp_wait<0>();
         }
-        __syncthreads();
+        tile_ok = __syncthreads_and(tile_ok) != 0;
+    }
+    if (!tile_ok) {
+#pragma unroll
+        for (int q = 0; q < NS; ++q) part[q] = 0.f;
+        return false;
     }
     if (valid) {
       if constexpr (POTTS && (MODE & kLean) != 0) {
@@ -553,6 +571,7 @@ __device__ __forceinline__ void pixel_chunk(const PixArgs &A, const FwLats &F, c
             }
         }
     }
+    return true;
 }
 
 // Label-split layout of the pixel pass (Lp = 24, Potts): three lanes per
@@ -769,10 +788,10 @@ __global__ void __launch_bounds__(PB, MB) k_fw_pixel(PixArgs A, FwLats F) {
         }
     }
     float part[NS];
-    pixel_chunk<LP, TB, POTTS, MODE>(A, F, ch, sy, sl, part, tbar);
+    const bool tile_ok = pixel_chunk<LP, TB, POTTS, MODE>(A, F, ch, sy, sl, part, tbar);
     if (tbar) fence_proxy_async_smem();   // y' rows written here are read by the bulk store
     __syncthreads();
-    if (A.alpha != nullptr) {
+    if (A.alpha != nullptr && tile_ok) {
         if (tbar) {
             if (threadIdx.x == 0)
                 bulk_s2g(A.Y + ch.begin * (int64_t)A.L, sy, (unsigned)(ch.count * A.L) * 4u);

@@ -3,7 +3,7 @@
 // The paper computes sum_b k(f_a, f_b) v_b with the permutohedral-lattice
 // filter it cites (Section 3 "Filter-based Method", Eq. 6; Appendix A), not
 // normalised.  Lattice conventions (scale, elevation, enclosing simplex,
-// blur, output scale) are the ones stated in include/dcrf.h and the design doc:
+// blur, output scale), shared with the CPU oracle:
 //   c_j   = f_j * alpha / sqrt((j+1)(j+2)),  alpha = (d+1) sqrt(2/3)
 //   x     = Helmert elevation onto sum(x) = 0 (FP64, one rounding per op)
 //   m_i   = rint(x_i / (d+1)), rank correction, barycentric weights
@@ -522,14 +522,24 @@ __global__ void k_slice(const T *__restrict__ V, int64_t n, int L, int G, int D1
     }
 }
 
-dcrf_status dcrf_slice_f32(const dcrf_lattice lat, const float *V, int Lp, int L, float *out, cudaStream_t s) {
+dcrf_status dcrf_slice(const dcrf_lattice lat, const void *V, int Lp, int L, int storage, float *out,
+                       cudaStream_t s) {
     if (lat->n == 0) return DCRF_OK;
     const int G = Lp / 4;
+    const unsigned nb = blocks_for(lat->n * G, 256);
     ProfScope ps(P_SLICE, s);
-    k_slice<float><<<blocks_for(lat->n * G, 256), 256, 0, s>>>(V, lat->n, L, G, lat->d + 1, lat->pvid, lat->pbary,
-                                                              (float)lat->s0, out);
+    if (storage == DCRF_STORAGE_F16)
+        k_slice<__half><<<nb, 256, 0, s>>>((const __half *)V, lat->n, L, G, lat->d + 1, lat->pvid, lat->pbary,
+                                           (float)lat->s0, out);
+    else
+        k_slice<float><<<nb, 256, 0, s>>>((const float *)V, lat->n, L, G, lat->d + 1, lat->pvid, lat->pbary,
+                                          (float)lat->s0, out);
     DCRF_LAUNCHED();
     return DCRF_OK;
+}
+
+dcrf_status dcrf_slice_f32(const dcrf_lattice lat, const float *V, int Lp, int L, float *out, cudaStream_t s) {
+    return dcrf_slice(lat, V, Lp, L, DCRF_STORAGE_F32, out, s);
 }
 
 static dcrf_status filter_impl(const dcrf_lattice lat, const float *Y, int L, float *out, int storage,
@@ -548,17 +558,7 @@ static dcrf_status filter_impl(const dcrf_lattice lat, const float *Y, int L, fl
     DCRF_TRY(cudaMemsetAsync(V, 0, (size_t)lat->m * Lp * sizeof(float), s));
     DCRF_CHECK_STATUS(dcrf_splat_dense(lat, Y, L, V, Lp, s));
     DCRF_CHECK_STATUS(dcrf_blur(lat, V, dst, tmp, Lp, storage, reverse, s));
-    const int G = Lp / 4;
-    const unsigned nb = blocks_for(lat->n * G, 256);
-    ProfScope ps(P_SLICE, s);
-    if (storage == DCRF_STORAGE_F16)
-        k_slice<__half><<<nb, 256, 0, s>>>((const __half *)dst, lat->n, L, G, lat->d + 1, lat->pvid, lat->pbary,
-                                           (float)lat->s0, out);
-    else
-        k_slice<float><<<nb, 256, 0, s>>>((const float *)dst, lat->n, L, G, lat->d + 1, lat->pvid, lat->pbary,
-                                          (float)lat->s0, out);
-    DCRF_LAUNCHED();
-    return DCRF_OK;
+    return dcrf_slice(lat, dst, Lp, L, storage, out, s);
 }
 
 extern "C" dcrf_status dcrf_filter(dcrf_lattice lat, const float *Y, int L, float *out, int storage,
@@ -812,6 +812,10 @@ extern "C" dcrf_status dcrf_lattice_build_batch(const float *features, const int
         lattice_free(lat);
         return st;
     }
+    // dcrf_filter_static's scratch address for this device, looked up here
+    // (outside any capture: the build synchronises) so that its calls find it
+    unsigned char *scratch = nullptr;
+    (void)dcrf_static_scratch(s, &scratch);
     *out = lat;
     return DCRF_OK;
 }

@@ -136,3 +136,24 @@ def test_fw_is_reproducible_bit_for_bit(dcrf):
         out.append((rec, Y.cpu().numpy()))
     np.testing.assert_array_equal(out[0][0], out[1][0])
     np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
+def test_bounded_wait_runs_out_and_the_context_survives(dcrf):
+    # The pixel pass waits for its tile copies with a bounded number of polls.
+    # The self-test arms an mbarrier for bytes that nothing sends (no copy in
+    # flight): the wait must run out, DCRF_E_TIMEOUT must reach the status
+    # word, and the next calls must run normally.
+    p = S.make_problem(24, 16, 3, 3, seed=90)
+    g = gpu_setup(dcrf, [p], torch)
+    dcrf.dcrf_selftest_bounded_wait(g["lb"], 1000, True)
+    with pytest.raises(dcrf.DcrfError) as ei:
+        g["lb"].status()
+    assert ei.value.status == -6
+    dcrf.dcrf_selftest_bounded_wait(g["lb"], 1000, False)
+    g["lb"].status()
+    out = dcrf.dcrf_filter(g["lb"], g["y0"]).cpu().numpy()
+    ref = P.Permutohedral(g["fb"].cpu().numpy()).filter(p.y0.astype(np.float64))
+    assert rel_err(out, ref) <= 1e-4
+    Y = g["y0"].clone()
+    rec = dcrf.dcrf_qp_fw(g["phi"], [g["lb"], g["ls"]], p.weights, Y, 5)
+    assert np.all(np.isfinite(rec))
