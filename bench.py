@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-all-cores", action="store_true")
     ap.add_argument("--no-lp", action="store_true")
+    ap.add_argument("--no-uneven", action="store_true", help="skip the uneven-size batch arm")
     ap.add_argument("--no-dcneg", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the CCCP and reverse-mode timings")
     return ap.parse_args()
@@ -153,6 +154,24 @@ def oracle_rate_all_cores(iters: int, workers: int):
     return workers * iters / max(dts), max(dts)
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def workload_config(B, W, H, T, storage):
     """The workload both arms report (the measured lattice sizes are added by ours)."""
     return {"workload": f"{B} x {W}x{H} synthetic VOC-shaped images per GPU, L=21, "
@@ -181,7 +200,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": workload_config(args.batch, args.width, args.height, args.iters, args.storage),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu_model": cpu_model(),
                          "sample": f"each step: {per_step} oracle FW iterations (FP64 numpy) on one "
                                    f"{args.width}x{args.height} image of the workload, scaled to image-iterations/s"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -395,25 +414,74 @@ def main():
                        "note": "kernels and roofline: a second pass over the same steps with per-launch CUDA "
                                "events (launched one by one, no graph replay)"}
 
-        # plain float32, one image, no batching
+        # the precision effect at equal batching, and the uneven batch: each
+        # arm timed like the headline (graph replay, CUDA events on the
+        # stream), then one instrumented step for its pixel-pass roofline
+        def arm(lats, phi_, y0_, storage, images, reps):
+            Ya = torch.empty_like(y0_)
+
+            def run():
+                Ya.copy_(y0_)
+                D.dcrf_qp_fw(phi_, lats, wts, Ya, T, storage=storage, records=False, stream=stream)
+
+            for _ in range(2):
+                run()
+            stream.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(reps):
+                run()
+            a1.record(stream)
+            stream.synchronize()
+            ms = a0.elapsed_time(a1) / reps
+            D.profile_enable(True)
+            run()
+            pr = D.profile_read()
+            D.profile_enable(False)
+            nn = y0_.shape[0]
+            cnt, kms = pr.get("fw_pixel", (0, 0.0))
+            out = {"value": images * T / (ms / 1000.0), "unit": UNIT, "ms_per_step": round(ms, 3),
+                   "pixel_iterations_per_s": nn * T / (ms / 1000.0)}
+            by = algorithmic_bytes("fw_pixel", nn, L, [lt.m for lt in lats], [lt.d for lt in lats], storage)
+            if cnt:
+                per_launch = by / T
+                gbs = per_launch / (kms / cnt / 1000.0) / 1e9
+                out["roofline"] = {"kernel": "fw_pixel", "bound": "hbm", "achieved": round(gbs, 1),
+                                   "peak": hbm_peak, "unit": "GB/s", "frac": round(gbs / hbm_peak, 4),
+                                   "peak_source": peak_src, "bytes_per_launch": int(per_launch),
+                                   "us_per_launch": round(1000 * kms / cnt, 2)}
+            return out
+
         p1 = [probs[0]]
         n1 = p1[0].n_pixels
         l1b = D.dcrf_lattice_build(fb[:n1].contiguous(), [0, n1], stream=stream)
         l1s = D.dcrf_lattice_build(fs[:n1].contiguous(), [0, n1], stream=stream)
-        Y1 = torch.empty_like(y0[:n1])
-        for _ in range(3):
-            Y1.copy_(y0[:n1])
-            D.dcrf_qp_fw(phi[:n1], [l1b, l1s], wts, Y1, T, storage="f32", records=False, stream=stream)
-        stream.synchronize()
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        reps = 5
-        for _ in range(reps):
-            Y1.copy_(y0[:n1])
-            D.dcrf_qp_fw(phi[:n1], [l1b, l1s], wts, Y1, T, storage="f32", records=False, stream=stream)
-        a1.record(stream)
-        stream.synchronize()
-        plain_fp32 = reps * T / (a0.elapsed_time(a1) / 1000.0)
+        single32 = arm([l1b, l1s], phi[:n1], y0[:n1], "f32", 1, 5)
+        plain_fp32 = single32["value"]
+        other = "f32" if args.storage == "f16" else "f16"
+        precision = {
+            "note": "lattice storage at equal batching: the batched arms run the headline batch, the single "
+                    "arms its first image alone",
+            f"batched_{args.storage}": {"value": value, "unit": UNIT, "ms_per_step": round(ms_step, 3)},
+            f"batched_{other}": arm([lb, ls], phi, y0, other, B, 3),
+            "single_image_f32": single32,
+            "single_image_f16": arm([l1b, l1s], phi[:n1], y0[:n1], "f16", 1, 5),
+        }
+        # the uneven batch: 32 images of W ~ U[240,500] x H ~ U[160,500]
+        uneven = None
+        if not args.no_uneven:
+            pu = S.make_batch(B, 0)
+            ou = np.concatenate([[0], np.cumsum([q.n_pixels for q in pu])]).astype(np.int64)
+            rgu = torch.from_numpy(np.concatenate([q.rgb.reshape(-1, 3) for q in pu])).to(dev)
+            fbu, fsu = D.dcrf_features(rgu, [q.width for q in pu], [q.height for q in pu], *th, stream=stream)
+            lub, lus = D.dcrf_lattice_build(fbu, ou, stream=stream), D.dcrf_lattice_build(fsu, ou, stream=stream)
+            phu = torch.from_numpy(np.concatenate([q.unaries for q in pu])).to(dev)
+            yu = torch.from_numpy(np.concatenate([q.y0 for q in pu])).to(dev)
+            uneven = dict(arm([lub, lus], phu, yu, args.storage, B, 3),
+                          workload=f"{B} synthetic images, W ~ U[240,500] x H ~ U[160,500] (seed 0), L=21, "
+                                   f"{args.storage} lattice storage, {T} Frank-Wolfe iterations per step",
+                          pixels=int(ou[-1]), vertices={"bilateral": lub.m, "spatial": lus.m})
+            del lub, lus
 
         # LP subgradient (sort + divide and conquer) on one 500x375 image, L=21
         lp = None
@@ -559,7 +627,7 @@ def main():
         r, dt, cores = oracle_rate(20)
         cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "20 oracle Frank-Wolfe iterations on one 500x375 image (FP64 numpy)",
-               "seconds": round(dt, 2)}
+               "seconds": round(dt, 2), "cpu_model": cpu_model(), "host_cores": os.cpu_count()}
         workers = os.cpu_count() or 1
         if workers > 1 and not args.no_cpu_all_cores:
             ra, dta = oracle_rate_all_cores(5, workers)
@@ -577,6 +645,8 @@ def main():
             "config": dict(workload_config(B, W_, H_, T, args.storage),
                            vertices={"bilateral": lb.m, "spatial": ls.m}, lattice_build_s=round(build_s, 4)),
             "plain_fp32_single_image": {"value": plain_fp32, "unit": UNIT},
+            "precision": precision,
+            "uneven_batch": uneven,
             "lp_subgrad": lp,
             "dc_neg": dcneg,
             "cccp": cccp,
