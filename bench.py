@@ -444,7 +444,7 @@ def main():
                    "pixel_iterations_per_s": nn * T / (ms / 1000.0)}
             by = algorithmic_bytes("fw_pixel", nn, L, [lt.m for lt in lats], [lt.d for lt in lats], storage)
             if cnt:
-                per_launch = by / T
+                per_launch = by                    # one pixel launch per iteration
                 gbs = per_launch / (kms / cnt / 1000.0) / 1e9
                 out["roofline"] = {"kernel": "fw_pixel", "bound": "hbm", "achieved": round(gbs, 1),
                                    "peak": hbm_peak, "unit": "GB/s", "frac": round(gbs / hbm_peak, 4),

@@ -147,9 +147,11 @@ def test_autograd_function_on_batch(dcrf, monkeypatch):
     # The one-hot splat sums fixed-point weights with integer reductions, so a
     # run does not depend on the order of the atomics, and an image of a batch
     # is processed exactly as alone when the same kernel variants run (forced
-    # here: the tuners may choose others for other sizes).  Every image then
-    # gets the gradient it gets alone up to the order of the FP64 reductions
-    # of the reverse sweep, and the weight gradient is the sum over images.
+    # here: the tuners may choose others for other sizes), so the decisions
+    # s^t agree.  The reverse sweep's filters still splat with float32
+    # atomics, so every image gets the gradient it gets alone to 1e-5, and the
+    # weight gradient, a sum over the images of terms that partly cancel, is
+    # their sum to the gradient tolerance 1e-4.
     from paper_1608_06192_gb300.autograd import FrankWolfeQP
     monkeypatch.setenv("DCRF_PIXEL_VARIANT", "14")
     monkeypatch.setenv("DCRF_BLUR_VARIANT", "0")
@@ -169,4 +171,4 @@ def test_autograd_function_on_batch(dcrf, monkeypatch):
         _, dphi_b, dw_b = _gpu_grad(dcrf, [probs[b]], ybar[s0:s1], 10)
         dw_sum += dw_b
         assert rel_err(dphi[s0:s1], dphi_b) <= 1e-5
-    assert rel_err(w.grad.numpy(), dw_sum) <= 1e-5
+    assert rel_err(w.grad.numpy(), dw_sum) <= 1e-4
