@@ -152,6 +152,11 @@ dcrf_status dcrf_blur(const dcrf_lattice lat, const float *src, void *dst, void 
 dcrf_status dcrf_slice(const dcrf_lattice lat, const void *V, int Lp, int L, int storage, float *out,
                        cudaStream_t s);
 dcrf_status dcrf_slice_f32(const dcrf_lattice lat, const float *V, int Lp, int L, float *out, cudaStream_t s);
+// Stable radix sort of (key, value) pairs inside host-given segments
+// [seg_begin[s], seg_begin[s+1]) by the low `bits` key bits (segsort.cu);
+// the result lands in kout/vout, ktmp/vtmp are scratch, kin/vin are read only.
+dcrf_status dcrf_segsort(const uint32_t *kin, const int32_t *vin, uint32_t *ktmp, int32_t *vtmp, uint32_t *kout,
+                         int32_t *vout, const int64_t *seg_begin, int nseg, int bits, cudaStream_t s);
 // Looks up, once per device, the device address of dcrf_filter_static's
 // array for the device of stream s (noalloc.cu).
 dcrf_status dcrf_static_scratch(cudaStream_t s, unsigned char **out);

@@ -22,6 +22,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
 
 #include "common.cuh"
 
@@ -35,8 +38,16 @@ inline int ceil_log2(int64_t n) {
     return b;
 }
 
-// keys[i][a] = y_a(i) (with -0 folded into +0), vals[i][a] = a
-__global__ void k_lp_transpose(const float *__restrict__ Y, int64_t n, int L, float *__restrict__ keys,
+// Sort key of a column value: ascending keys = descending values (-0 is
+// folded into +0 first, so equal values get equal keys and keep pixel order).
+__device__ __forceinline__ uint32_t desc_key(float v) {
+    const uint32_t b = __float_as_uint(v + 0.0f);
+    const uint32_t asc = (b & 0x80000000u) ? ~b : (b | 0x80000000u);   // ascending order of the floats
+    return ~asc;
+}
+
+// keys[i][a] = key of y_a(i), vals[i][a] = a
+__global__ void k_lp_transpose(const float *__restrict__ Y, int64_t n, int L, uint32_t *__restrict__ keys,
                                int32_t *__restrict__ vals, int *status) {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= n * L) return;
@@ -44,14 +55,14 @@ __global__ void k_lp_transpose(const float *__restrict__ Y, int64_t n, int L, fl
     const int i = (int)(q - a * L);
     float v = Y[q];
     if (!isfinite(v)) dcrf_flag(status, DCRF_E_NONFINITE);
-    keys[(int64_t)i * n + a] = v + 0.0f;
+    keys[(int64_t)i * n + a] = desc_key(v);
     vals[(int64_t)i * n + a] = (int32_t)a;
 }
 
 // Tree columns (Appendix F): keys[t][a] = y_a(T_t) = sum of y_a(i) over the
 // labels i of subtree t (bit i of mask[t]), in label order; vals[t][a] = a
 __global__ void k_lp_columns(const float *__restrict__ Y, int64_t n, int L, int C, const uint64_t *__restrict__ mask,
-                             float *__restrict__ keys, int32_t *__restrict__ vals, int *status) {
+                             uint32_t *__restrict__ keys, int32_t *__restrict__ vals, int *status) {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= n * C) return;
     const int64_t a = q / C;
@@ -61,7 +72,7 @@ __global__ void k_lp_columns(const float *__restrict__ Y, int64_t n, int L, int 
     for (int i = 0; i < L; ++i)
         if ((mk >> i) & 1ull) v += Y[a * L + i];
     if (!isfinite(v)) dcrf_flag(status, DCRF_E_NONFINITE);
-    keys[(int64_t)t * n + a] = v + 0.0f;
+    keys[(int64_t)t * n + a] = desc_key(v);
     vals[(int64_t)t * n + a] = (int32_t)a;
 }
 
@@ -83,9 +94,10 @@ __global__ void k_lp_inverse(const int32_t *__restrict__ perm, int64_t n, int L,
     inv[i * n + perm[q]] = (int32_t)(q - i * n);
 }
 
-// Entries in (label, position, corner) order: key = label * M + vertex.
+// Entries in (label, position, corner) order: key = vertex (the entries of
+// one (label, image) are sorted by it, stably).
 __global__ void k_lp_entries(const int32_t *__restrict__ perm, int64_t n, int L, int d1,
-                             const int32_t *__restrict__ pvid, int64_t m, uint64_t *__restrict__ key,
+                             const int32_t *__restrict__ pvid, int64_t m, uint32_t *__restrict__ key,
                              int32_t *__restrict__ q_out) {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t E = n * L * d1;
@@ -95,12 +107,14 @@ __global__ void k_lp_entries(const int32_t *__restrict__ perm, int64_t n, int L,
     const int64_t i = ip / n;
     const int32_t a = perm[ip];
     const int v = pvid[(int64_t)a * d1 + k];
-    key[q] = (uint64_t)i * (uint64_t)m + (uint64_t)(v < 0 ? 0 : v);
+    (void)i;
+    (void)m;
+    key[q] = (uint32_t)(v < 0 ? 0 : v);
     q_out[q] = (int32_t)q;
 }
 
 // After the sort: per entry its vertex, rank, weight, and pos[q] = e.
-__global__ void k_lp_unpack(const uint64_t *__restrict__ key_s, const int32_t *__restrict__ q_s, int64_t E,
+__global__ void k_lp_unpack(const uint32_t *__restrict__ key_s, const int32_t *__restrict__ q_s, int64_t E,
                             int64_t n, int d1, int64_t m, const int32_t *__restrict__ perm,
                             const int64_t *__restrict__ point_off, int batch, const float *__restrict__ pbary,
                             int32_t *__restrict__ vid_s, int32_t *__restrict__ rank_s,
@@ -117,7 +131,8 @@ __global__ void k_lp_unpack(const uint64_t *__restrict__ key_s, const int32_t *_
         int mid = (lo + hi + 1) >> 1;
         if (point_off[mid] <= p) lo = mid; else hi = mid - 1;
     }
-    vid_s[e] = (int32_t)(key_s[e] % (uint64_t)m);
+    (void)m;
+    vid_s[e] = (int32_t)key_s[e];
     rank_s[e] = (int32_t)(p - point_off[lo]);
     bary_s[e] = pbary[(int64_t)a * d1 + k];
     pos[q] = (int32_t)e;
@@ -601,13 +616,17 @@ struct LpWork {
     size_t lblocks_cap = 0;
     int maxlev = 0;
     float *c = nullptr;
-    float *keys = nullptr, *keys2 = nullptr;
-    int32_t *vals = nullptr, *perm = nullptr, *inv = nullptr;
+    uint32_t *keys = nullptr, *keys2 = nullptr, *keys3 = nullptr;
+    int32_t *vals = nullptr, *vals2 = nullptr, *perm = nullptr, *inv = nullptr;
+    std::vector<int64_t> colseg;      // host [C * batch + 1]: segments (column, image) of the sorted columns
+    std::vector<int64_t> entseg[DCRF_MAX_KERNELS];   // host: segments (column, image) of the entries
+    bool cub_sort = false;            // DCRF_LP_SORT=cub: CUB's radix sorts (a test comparator)
     float *U = nullptr;
     int64_t *csr[DCRF_MAX_KERNELS] = {};
     int64_t Emax = 0;
-    uint64_t *ekey = nullptr, *ekey2 = nullptr;
-    int32_t *eq = nullptr, *eq2 = nullptr, *vid_s = nullptr, *rank_s = nullptr, *pos = nullptr;
+    uint32_t *ekey = nullptr, *ekey2 = nullptr, *ekey3 = nullptr;
+    int32_t *eq = nullptr, *eq2 = nullptr, *eq3 = nullptr, *vid_s = nullptr, *rank_s = nullptr, *pos = nullptr;
+    int64_t *eseg_b = nullptr, *eseg_e = nullptr;   // device segment bounds of the entries (CUB comparator)
     int32_t *flag = nullptr, *rid = nullptr, *run_first = nullptr, *rnbr = nullptr;
     float *bary_s = nullptr, *val = nullptr, *val2 = nullptr;
     void *tmp = nullptr;
@@ -687,15 +706,34 @@ struct LpWork {
         DCRF_CHECK_STATUS(sc.get(&c, (size_t)(n > 0 ? n : 1)));
         DCRF_CHECK_STATUS(sc.get(&keys, nl));
         DCRF_CHECK_STATUS(sc.get(&keys2, nl));
+        DCRF_CHECK_STATUS(sc.get(&keys3, nl));
         DCRF_CHECK_STATUS(sc.get(&vals, nl));
+        DCRF_CHECK_STATUS(sc.get(&vals2, nl));
         DCRF_CHECK_STATUS(sc.get(&perm, nl));
         DCRF_CHECK_STATUS(sc.get(&inv, nl));
         DCRF_CHECK_STATUS(sc.get(&U, nl));
         const size_t ne = (size_t)(Emax > 0 ? Emax : 1);
         DCRF_CHECK_STATUS(sc.get(&ekey, ne));
         DCRF_CHECK_STATUS(sc.get(&ekey2, ne));
+        DCRF_CHECK_STATUS(sc.get(&ekey3, ne));
         DCRF_CHECK_STATUS(sc.get(&eq, ne));
         DCRF_CHECK_STATUS(sc.get(&eq2, ne));
+        DCRF_CHECK_STATUS(sc.get(&eq3, ne));
+        // sort segments: every (column, image) of the sorted columns, and of
+        // the entries (d+1 per position)
+        const std::vector<int64_t> &po = lattices[0]->point_off;
+        colseg.clear();
+        for (int i = 0; i < C; ++i)
+            for (int b = 0; b < batch; ++b) colseg.push_back((int64_t)i * n + po[b]);
+        colseg.push_back((int64_t)C * n);
+        for (int m = 0; m < nk; ++m) {
+            entseg[m].clear();
+            for (int64_t x : colseg) entseg[m].push_back(x * (lattices[m]->d + 1));
+        }
+        const char *srt = std::getenv("DCRF_LP_SORT");
+        cub_sort = srt && std::strcmp(srt, "cub") == 0;
+        DCRF_CHECK_STATUS(sc.get(&eseg_b, (size_t)C * batch));
+        DCRF_CHECK_STATUS(sc.get(&eseg_e, (size_t)C * batch));
         DCRF_CHECK_STATUS(sc.get(&vid_s, ne));
         DCRF_CHECK_STATUS(sc.get(&rank_s, ne));
         DCRF_CHECK_STATUS(sc.get(&pos, ne));
@@ -710,9 +748,10 @@ struct LpWork {
         DCRF_CHECK_STATUS(sc.get(&rnbr, ne * dmax * 2));
         // temp storage for the sorts and scans
         size_t t1 = 0, t2 = 0, t3 = 0;
-        DCRF_TRY(cub::DeviceSegmentedRadixSort::SortPairsDescending(nullptr, t1, keys, keys2, vals, perm, (int)nl,
-                                                                     C * batch, seg_b, seg_e, 0, 32, s));
-        DCRF_TRY(cub::DeviceRadixSort::SortPairs(nullptr, t2, ekey, ekey2, eq, eq2, (int)ne, 0, 64, s));
+        DCRF_TRY(cub::DeviceSegmentedRadixSort::SortPairs(nullptr, t1, keys, keys2, vals, perm, (int)nl, C * batch,
+                                                          seg_b, seg_e, 0, 32, s));
+        DCRF_TRY(cub::DeviceSegmentedRadixSort::SortPairs(nullptr, t2, ekey, ekey2, eq, eq2, (int)ne, C * batch,
+                                                          eseg_b, eseg_e, 0, 32, s));
         DCRF_TRY(cub::DeviceScan::InclusiveSum(nullptr, t3, flag, rid, (int)ne, s));
         tmp_bytes = std::max(t1, std::max(t2, t3));
         char *t;
@@ -762,9 +801,14 @@ struct LpWork {
             else
                 k_lp_transpose<<<nb(nl, 256), 256, 0, s>>>(Y, n, L, keys, vals, lats[0]->status);
             DCRF_LAUNCHED();
-            size_t tb = tmp_bytes;
-            DCRF_TRY(cub::DeviceSegmentedRadixSort::SortPairsDescending(tmp, tb, keys, keys2, vals, perm, (int)nl,
-                                                                         C * batch, seg_b, seg_e, 0, 32, s));
+            if (cub_sort) {
+                size_t tb = tmp_bytes;
+                DCRF_TRY(cub::DeviceSegmentedRadixSort::SortPairs(tmp, tb, keys, keys2, vals, perm, (int)nl,
+                                                                  C * batch, seg_b, seg_e, 0, 32, s));
+            } else {
+                DCRF_CHECK_STATUS(dcrf_segsort(keys, vals, keys3, vals2, keys2, perm, colseg.data(), C * batch, 32,
+                                               s));
+            }
             k_lp_inverse<<<nb(nl, 256), 256, 0, s>>>(perm, n, C, inv);
             DCRF_LAUNCHED();
         }
@@ -775,13 +819,23 @@ struct LpWork {
             const int64_t E = nl * d1;
             const int64_t m = lat->m > 0 ? lat->m : 1;
             int keybits = 1;
-            while (keybits < 64 && ((uint64_t)C * (uint64_t)m) > (1ull << keybits)) ++keybits;
+            while (keybits < 32 && (uint64_t)m > (1ull << keybits)) ++keybits;
             {
                 ProfScope ps(P_LP_SORT, s);
                 k_lp_entries<<<nb(E, 256), 256, 0, s>>>(perm, n, C, d1, lat->pvid, m, ekey, eq);
                 DCRF_LAUNCHED();
-                size_t tb = tmp_bytes;
-                DCRF_TRY(cub::DeviceRadixSort::SortPairs(tmp, tb, ekey, ekey2, eq, eq2, (int)E, 0, keybits, s));
+                if (cub_sort) {
+                    std::vector<int64_t> eb(entseg[mm].begin(), entseg[mm].end() - 1),
+                        ee(entseg[mm].begin() + 1, entseg[mm].end());
+                    DCRF_TRY(cudaMemcpyAsync(eseg_b, eb.data(), eb.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+                    DCRF_TRY(cudaMemcpyAsync(eseg_e, ee.data(), ee.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+                    size_t tb = tmp_bytes;
+                    DCRF_TRY(cub::DeviceSegmentedRadixSort::SortPairs(tmp, tb, ekey, ekey2, eq, eq2, (int)E, C * batch,
+                                                                      eseg_b, eseg_e, 0, keybits, s));
+                } else {
+                    DCRF_CHECK_STATUS(dcrf_segsort(ekey, eq, ekey3, eq3, ekey2, eq2, entseg[mm].data(), C * batch,
+                                                   keybits, s));
+                }
                 k_lp_unpack<<<nb(E, 256), 256, 0, s>>>(ekey2, eq2, E, n, d1, m, perm, off_d, batch, lat->pbary,
                                                        vid_s, rank_s, bary_s, pos);
                 DCRF_LAUNCHED();

@@ -77,9 +77,11 @@ def test_lp_solve_small(dcrf):
 
 
 def test_lp_solve_headline_200_steps(dcrf):
-    # 200 projected-subgradient steps at 500x375, L=21 (no oracle at this size:
-    # the iterate stays on the simplex, every energy is finite, the best
-    # energy does not exceed the start and the returned y has that energy)
+    # 200 projected-subgradient steps at 500x375, L=21 (the oracle's 200 steps
+    # at this size would take hours; the subgradient itself is checked at
+    # this size above: the iterate stays on the simplex, every energy is
+    # finite, the best energy does not exceed the start and the returned y
+    # has that energy)
     p = S.voc_shaped()
     g = gpu_setup(dcrf, [p], torch)
     y0 = S.dirichlet_labels(p.n_pixels, 21, seed=11)
@@ -92,3 +94,40 @@ def test_lp_solve_headline_200_steps(dcrf):
     assert Yg.min() >= 0.0
     _, e_best = dcrf.dcrf_lp_subgrad(g["phi"], Y, [g["lb"], g["ls"]], p.weights)
     assert abs(e_best[0] - e.min()) <= 1e-3 * abs(e.min())
+
+
+def test_lp_subgrad_full_size_two_columns(dcrf):
+    # 500x375, L=21, y ~ Dirichlet(0.5): the sorted columns of labels 0 and 20
+    # through all 18 levels of the divide and conquer, against the oracle
+    p = S.voc_shaped()
+    g = gpu_setup(dcrf, [p], torch)
+    y = S.dirichlet_labels(p.n_pixels, 21, seed=5)
+    G, _ = dcrf.dcrf_lp_subgrad(g["phi"], torch.from_numpy(y).cuda(), [g["lb"], g["ls"]], p.weights)
+    G = G.cpu().numpy()
+    c = oracle_crf(p)
+    for i in (0, 20):
+        U = lp.upper_sums_dc(lp.label_rank(y[:, i].astype(np.float64)), c.kernel.apply_partitioned)
+        assert rel_err(G[:, i], c.phi[:, i] + 2.0 * U - c.c) <= 1e-4
+
+
+@pytest.mark.parametrize("shape", [(120, 90, 21), (37, 23, 4)])
+def test_lp_own_sort_matches_cub(dcrf, shape, monkeypatch):
+    # the per-label sort and the grouping of incidences by vertex are the
+    # library's own segmented radix sort; CUB's radix sort, switched on by
+    # DCRF_LP_SORT=cub, is the comparator: both are stable with the same key
+    # order, so the subgradients agree up to the order of the float atomics
+    # that sum the lattice values
+    W, H, L = shape
+    probs = [S.make_problem(W, H, 6, L, seed=20), S.make_problem(W // 2 + 1, H, 6, L, seed=21)]
+    ys = [S.dirichlet_labels(q.n_pixels, L, seed=22 + i) for i, q in enumerate(probs)]
+    ys[0][::5] = 1.0 / L                              # exact ties, kept in pixel order
+    g = gpu_setup(dcrf, probs, torch)
+    Y = torch.from_numpy(np.concatenate(ys)).cuda()
+    G1, e1 = dcrf.dcrf_lp_subgrad(g["phi"], Y, [g["lb"], g["ls"]], probs[0].weights)
+    monkeypatch.setenv("DCRF_LP_SORT", "cub")
+    G2, e2 = dcrf.dcrf_lp_subgrad(g["phi"], Y, [g["lb"], g["ls"]], probs[0].weights)
+    assert rel_err(G1.cpu().numpy(), G2.cpu().numpy()) <= 1e-6
+    np.testing.assert_allclose(e1, e2, rtol=1e-6)
+    for b, (p, y) in enumerate(zip(probs, ys)):
+        s, t = g["off"][b], g["off"][b + 1]
+        assert rel_err(G1.cpu().numpy()[s:t], _oracle_subgrad(p, y)) <= 1e-4
