@@ -285,26 +285,45 @@ def measured_traffic(kind, n):
         return None
 
 
+def lp_algorithmic_bytes(n, L, levels, lat_d):
+    """Bytes one LP subgradient must move at least (a lower bound: the blur of
+    the tagged vertices is left out, their count depends on the level).
+
+    Per label and level and lattice (d+1 corners per point): the tagged keys
+    of the node lattices (16 B per incidence), the splat of the right child
+    (vertex id + weight, 8 B per incidence), the slice at the left child
+    (8 B per incidence) and the point's upper sum U (read + write, 8 B).  Per
+    label once: the column sort (key + value read and written, 16 B per
+    point) and G (y, phi read, G written: 12 B per point).
+    """
+    per_level = sum(n * ((d + 1) * 32 + 8) for d in lat_d)
+    return L * (levels * per_level + 28 * n)
+
+
 def algorithmic_bytes(kind, n, L, lat_m, lat_d, storage):
     """Bytes one Frank-Wolfe iteration must move for a kernel kind (all launches of it).
 
     Per pixel: y read+write and (phi - d) read (12 L), s read+write and c (6),
     vertex id + weight per simplex corner (8 (d+1) per lattice).  Per lattice
-    vertex row of Lp labels: the one-hot splat S s in float32 (4),
+    vertex row of Lp labels: the one-hot splat S s in 32-bit fixed point (4),
     B S s and the sliced B S y in the storage type (esz), Ylat and BY in float32.
+    The splat reads the incidences grouped by vertex (point + weight, 8 B per
+    simplex corner), s once, the vertex offsets, and writes its rows.
     """
     Lp = 8 if L <= 8 else (24 if L <= 24 else 64)
     esz = 2 if storage == "f16" else 4
     half_copy = 2 if storage == "f16" else 0
     if kind == "fw_pixel":
         per_px = 12 * L + 6 + sum(8 * (d + 1) for d in lat_d)
-        return n * per_px + sum(m * Lp * (esz + 4) for m in lat_m)
+        return n * per_px + sum(m * Lp * esz for m in lat_m)
+    if kind == "fw_splat":
+        return sum(n * (d + 1) * 8 + n + m * (4 * Lp + 4) for m, d in zip(lat_m, lat_d))
     if kind == "fw_blur":
         return sum(m * Lp * (4 + esz) + d * m * Lp * 2 * esz + (d + 1) * 8 * m for m, d in zip(lat_m, lat_d))
     if kind == "fw_latdot":
         return sum(m * Lp * (8 + esz) for m in lat_m)
     if kind == "fw_latupd":
-        return sum(m * Lp * (24 + esz + half_copy) + 4 * m for m in lat_m)
+        return sum(m * Lp * (20 + esz + half_copy) + 4 * m for m in lat_m)
     return 0
 
 
@@ -391,7 +410,7 @@ def main():
 
         # roofline of the dominant kernel (CUDA events on the launching stream)
         lat_m, lat_d = [lb.m, ls.m], [5, 2]
-        per_iter_launch = {"fw_pixel": 1, "fw_blur": max(lat_d) + 1, "fw_latdot": 2, "fw_latupd": 2}
+        per_iter_launch = {"fw_pixel": 1, "fw_splat": 1, "fw_blur": max(lat_d) + 1, "fw_latdot": 2, "fw_latupd": 2}
         roof = None
         kinds = {}
         for kind, (cnt, ms) in prof.items():
@@ -520,9 +539,23 @@ def main():
             c1.record(stream)
             stream.synchronize()
             kt_ms = c0.elapsed_time(c1) / reps_lp
+            # 200 projected-subgradient steps (Algorithm 3) from the same point
+            Ys = y_lp.clone()
+            c0.record(stream)
+            D.dcrf_lp_solve(phi[:n1], [l1b, l1s], wts, Ys, 200, energies=False, stream=stream)
+            c1.record(stream)
+            stream.synchronize()
+            solve_ms = c0.elapsed_time(c1)
+            lp_bytes = lp_algorithmic_bytes(n1, L, nlev, [l1b.d, l1s.d])
+            lp_gbs = lp_bytes / (lp_ms / 1000.0) / 1e9
             lp = {"workload": "one 500x375 image, L=21, y ~ Dirichlet(0.5), bilateral + spatial lattices",
                   "ms_per_subgradient": round(lp_ms, 3), "subgradients_per_s": round(1000.0 / lp_ms, 2),
                   "label_levels_per_s": round(L * nlev * 1000.0 / lp_ms, 1),
+                  "effective_GBps": round(lp_gbs, 1), "bytes_per_subgradient": int(lp_bytes),
+                  "roofline": {"bound": "hbm", "achieved": round(lp_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                               "frac": round(lp_gbs / hbm_peak, 4), "peak_source": peak_src},
+                  "projected_subgradient_200_steps": {"ms": round(solve_ms, 1),
+                                                      "ms_per_step": round(solve_ms / 200, 3)},
                   "tree_metric": {"tree": "r-HST, r=2: 2 halves, groups of 4, %d leaves (%d subtrees)"
                                           % (L, len(c_t)),
                                   "ms_per_subgradient": round(tree_ms, 3),

@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(1024) k_fw_alpha(PartSums P, double *alpha, dc
     }
 }
 
-// Ylat += alpha (Slat - Ylat); BY += alpha (BS - BY) (and its half copy); Sq = 0.
+// Ylat += alpha (Slat - Ylat); BY += alpha (BS - BY) (and its half copy).
 template <typename T>
 __global__ void k_fw_latupd(FwLat lt, int G, const double *alpha) {
     int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -491,7 +491,57 @@ __global__ void k_fw_latupd(FwLat lt, int G, const double *alpha) {
     st4(lt.Ylat, idx, y);
     st4(lt.BY, idx, by);
     if (lt.BYh) st4h(lt.BYh, idx, by);
-    reinterpret_cast<uint4 *>(lt.Sq)[idx] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// One-hot splat S s of every lattice (App. B's one filter per iteration
+// starts from the splat of the vertex s): Sq[v][c] = sum over the incidences
+// (a, b) of vertex v with s_a = c of round(2^k b).  One warp per vertex (a
+// grid-stride loop over the vertices of all lattices): lanes take the
+// incidences, add into the warp's shared row with integer atomics (exact, so
+// the order does not matter), and the row is stored whole; every entry is
+// written, so Sq needs no clearing between iterations.
+struct SplatSet {
+    const int32_t *off[DCRF_MAX_KERNELS];
+    const int2 *inc[DCRF_MAX_KERNELS];
+    uint32_t *Sq[DCRF_MAX_KERNELS];
+    const float *qs[DCRF_MAX_KERNELS];
+    int64_t start[DCRF_MAX_KERNELS + 1];   // prefix of the vertex counts
+    int nk;
+};
+constexpr int kSplatWarps = 8;
+
+template <int LP>
+__global__ void __launch_bounds__(32 * kSplatWarps) k_fw_splat(SplatSet P, const uint8_t *__restrict__ s) {
+    __shared__ uint32_t row[kSplatWarps][LP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t total = P.start[P.nk];
+    const int64_t stride = (int64_t)gridDim.x * kSplatWarps;
+    for (int64_t g = (int64_t)blockIdx.x * kSplatWarps + w; g < total; g += stride) {
+        int mm = 0;
+#pragma unroll
+        for (int k = 1; k < DCRF_MAX_KERNELS; ++k)
+            if (k < P.nk && g >= P.start[k]) mm = k;
+        const int32_t *off = P.off[0];
+        const int2 *inc = P.inc[0];
+        uint32_t *Sq = P.Sq[0];
+        const float *qs = P.qs[0];
+#pragma unroll
+        for (int k = 1; k < DCRF_MAX_KERNELS; ++k)
+            if (k == mm) { off = P.off[k]; inc = P.inc[k]; Sq = P.Sq[k]; qs = P.qs[k]; }
+        const int64_t v = g - P.start[mm];
+        for (int c = lane; c < LP; c += 32) row[w][c] = 0u;
+        __syncwarp();
+        const float q = __ldg(qs);
+        const int e1 = off[v + 1];
+        for (int e = off[v] + lane; e < e1; e += 32) {
+            const int2 p = inc[e];
+            const unsigned c = s[p.x];
+            if (c < (unsigned)LP) atomicAdd(&row[w][c], __float2uint_rn(q * __int_as_float(p.y)));
+        }
+        __syncwarp();
+        for (int c = lane; c < LP; c += 32) Sq[v * LP + c] = row[w][c];
+        __syncwarp();
+    }
 }
 
 // Decision trace: row *counter of trace (when below rows) receives s, the
@@ -693,6 +743,8 @@ struct Solver {
             l.pvid = lat->pvid;
             l.pbary = lat->pbary;
             l.vimg = lat->vimg;
+            l.inc_off = lat->inc_off;
+            l.inc = lat->inc;
             l.m = lat->m;
             l.d1 = lat->d + 1;
             l.ws0 = (float)(weights[m] * lat->s0);
@@ -978,12 +1030,51 @@ struct Solver {
         return pixel_t<64, T, POT>(Y, phi, start);
     }
 
+    // The one-hot splat of s into Sq for every lattice (after a pixel pass).
+    template <int LPc>
+    dcrf_status splat_t() {
+        SplatSet P{};
+        P.nk = nk;
+        P.start[0] = 0;
+        for (int m = 0; m < nk; ++m) {
+            P.off[m] = F.l[m].inc_off;
+            P.inc[m] = F.l[m].inc;
+            P.Sq[m] = F.l[m].Sq;
+            P.qs[m] = F.l[m].qs;
+            P.start[m + 1] = P.start[m] + F.l[m].m;
+        }
+        if (P.start[nk] == 0) return DCRF_OK;
+        static int grid = 0;
+        if (grid == 0) {
+            int dev = 0, sms = 1, per_sm = 1;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fw_splat<LPc>, 32 * kSplatWarps, 0) !=
+                    cudaSuccess)
+                grid = 1024;
+            else
+                grid = std::max(1, sms * std::max(1, per_sm));
+        }
+        const int64_t need = (P.start[nk] + kSplatWarps - 1) / kSplatWarps;
+        ProfScope ps(P_FW_SPLAT, s);
+        k_fw_splat<LPc><<<(unsigned)std::min<int64_t>(need, grid), 32 * kSplatWarps, 0, s>>>(P, sidx);
+        DCRF_LAUNCHED();
+        return DCRF_OK;
+    }
+
+    dcrf_status splat() {
+        if (Lp == 8) return splat_t<8>();
+        if (Lp == 24) return splat_t<24>();
+        return splat_t<64>();
+    }
+
     dcrf_status pixel(float *Y, const float *phi, bool start) {
         dcrf_status st;
         if (storage == DCRF_STORAGE_F16)
             st = potts ? pixel_lp<__half, true>(Y, phi, start) : pixel_lp<__half, false>(Y, phi, start);
         else
             st = potts ? pixel_lp<float, true>(Y, phi, start) : pixel_lp<float, false>(Y, phi, start);
+        if (st == DCRF_OK && n > 0) st = splat();
         if (st != DCRF_OK || !trace || n == 0) return st;
         k_fw_trace<<<(unsigned)std::min<int64_t>(nblocks(n, 256), 4096), 256, 0, s>>>(sidx, trace, counter, n,
                                                                                       trace_rows);
