@@ -495,53 +495,63 @@ __global__ void k_fw_latupd(FwLat lt, int G, const double *alpha) {
 
 // One-hot splat S s of every lattice (App. B's one filter per iteration
 // starts from the splat of the vertex s): Sq[v][c] = sum over the incidences
-// (a, b) of vertex v with s_a = c of round(2^k b).  One warp per vertex (a
-// grid-stride loop over the vertices of all lattices): lanes take the
-// incidences, add into the warp's shared row with integer atomics (exact, so
-// the order does not matter), and the row is stored whole; every entry is
-// written, so Sq needs no clearing between iterations.
+// (a, b) of vertex v with s_a = c of round(2^k b).  One block per run of
+// kSplatVerts consecutive vertices of one lattice: the block's threads stride
+// over the run's incidences (contiguous, grouped by vertex), find each one's
+// vertex by binary search in the run's offsets, and add into the block's
+// shared rows with integer atomics (exact, so the order does not matter);
+// the rows are then stored whole.  Every entry is written, so Sq needs no
+// clearing between iterations.
 struct SplatSet {
     const int32_t *off[DCRF_MAX_KERNELS];
     const int2 *inc[DCRF_MAX_KERNELS];
     uint32_t *Sq[DCRF_MAX_KERNELS];
     const float *qs[DCRF_MAX_KERNELS];
-    int64_t start[DCRF_MAX_KERNELS + 1];   // prefix of the vertex counts
+    int64_t m[DCRF_MAX_KERNELS];
+    int64_t bstart[DCRF_MAX_KERNELS + 1];   // prefix of the block counts
     int nk;
 };
-constexpr int kSplatWarps = 8;
+constexpr int kSplatVerts = 128;
+constexpr int kSplatThreads = 256;
 
 template <int LP>
-__global__ void __launch_bounds__(32 * kSplatWarps) k_fw_splat(SplatSet P, const uint8_t *__restrict__ s) {
-    __shared__ uint32_t row[kSplatWarps][LP];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t total = P.start[P.nk];
-    const int64_t stride = (int64_t)gridDim.x * kSplatWarps;
-    for (int64_t g = (int64_t)blockIdx.x * kSplatWarps + w; g < total; g += stride) {
-        int mm = 0;
+__global__ void __launch_bounds__(kSplatThreads) k_fw_splat(SplatSet P, const uint8_t *__restrict__ s) {
+    __shared__ uint32_t rows[kSplatVerts * LP];
+    __shared__ int32_t soff[kSplatVerts + 1];
+    const int64_t blk = blockIdx.x;
+    int mm = 0;
 #pragma unroll
-        for (int k = 1; k < DCRF_MAX_KERNELS; ++k)
-            if (k < P.nk && g >= P.start[k]) mm = k;
-        const int32_t *off = P.off[0];
-        const int2 *inc = P.inc[0];
-        uint32_t *Sq = P.Sq[0];
-        const float *qs = P.qs[0];
+    for (int k = 1; k < DCRF_MAX_KERNELS; ++k)
+        if (k < P.nk && blk >= P.bstart[k]) mm = k;
+    const int32_t *off = P.off[0];
+    const int2 *inc = P.inc[0];
+    uint32_t *Sq = P.Sq[0];
+    const float *qs = P.qs[0];
+    int64_t m = P.m[0];
 #pragma unroll
-        for (int k = 1; k < DCRF_MAX_KERNELS; ++k)
-            if (k == mm) { off = P.off[k]; inc = P.inc[k]; Sq = P.Sq[k]; qs = P.qs[k]; }
-        const int64_t v = g - P.start[mm];
-        for (int c = lane; c < LP; c += 32) row[w][c] = 0u;
-        __syncwarp();
-        const float q = __ldg(qs);
-        const int e1 = off[v + 1];
-        for (int e = off[v] + lane; e < e1; e += 32) {
-            const int2 p = inc[e];
-            const unsigned c = s[p.x];
-            if (c < (unsigned)LP) atomicAdd(&row[w][c], __float2uint_rn(q * __int_as_float(p.y)));
+    for (int k = 1; k < DCRF_MAX_KERNELS; ++k)
+        if (k == mm) { off = P.off[k]; inc = P.inc[k]; Sq = P.Sq[k]; qs = P.qs[k]; m = P.m[k]; }
+    const int64_t v0 = (blk - P.bstart[mm]) * kSplatVerts;
+    const int nv = (int)min((int64_t)kSplatVerts, m - v0);
+    for (int i = threadIdx.x; i <= nv; i += kSplatThreads) soff[i] = off[v0 + i];
+    for (int i = threadIdx.x; i < nv * LP; i += kSplatThreads) rows[i] = 0u;
+    __syncthreads();
+    const int e0 = soff[0], e1 = soff[nv];
+    const float q = __ldg(qs);
+#pragma unroll 4
+    for (int e = e0 + threadIdx.x; e < e1; e += kSplatThreads) {
+        const int2 p = inc[e];
+        const unsigned c = s[p.x];
+        int lo = 0, hi = nv - 1;   // the last local vertex whose incidences start at or before e
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (soff[mid] <= e) lo = mid; else hi = mid - 1;
         }
-        __syncwarp();
-        for (int c = lane; c < LP; c += 32) Sq[v * LP + c] = row[w][c];
-        __syncwarp();
+        if (c < (unsigned)LP) atomicAdd(&rows[lo * LP + c], __float2uint_rn(q * __int_as_float(p.y)));
     }
+    __syncthreads();
+    uint32_t *dst = Sq + v0 * LP;
+    for (int i = threadIdx.x; i < nv * LP; i += kSplatThreads) dst[i] = rows[i];
 }
 
 // Decision trace: row *counter of trace (when below rows) receives s, the
@@ -1035,29 +1045,18 @@ struct Solver {
     dcrf_status splat_t() {
         SplatSet P{};
         P.nk = nk;
-        P.start[0] = 0;
+        P.bstart[0] = 0;
         for (int m = 0; m < nk; ++m) {
             P.off[m] = F.l[m].inc_off;
             P.inc[m] = F.l[m].inc;
             P.Sq[m] = F.l[m].Sq;
             P.qs[m] = F.l[m].qs;
-            P.start[m + 1] = P.start[m] + F.l[m].m;
+            P.m[m] = F.l[m].m;
+            P.bstart[m + 1] = P.bstart[m] + (F.l[m].m + kSplatVerts - 1) / kSplatVerts;
         }
-        if (P.start[nk] == 0) return DCRF_OK;
-        static int grid = 0;
-        if (grid == 0) {
-            int dev = 0, sms = 1, per_sm = 1;
-            if (cudaGetDevice(&dev) != cudaSuccess ||
-                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fw_splat<LPc>, 32 * kSplatWarps, 0) !=
-                    cudaSuccess)
-                grid = 1024;
-            else
-                grid = std::max(1, sms * std::max(1, per_sm));
-        }
-        const int64_t need = (P.start[nk] + kSplatWarps - 1) / kSplatWarps;
+        if (P.bstart[nk] == 0) return DCRF_OK;
         ProfScope ps(P_FW_SPLAT, s);
-        k_fw_splat<LPc><<<(unsigned)std::min<int64_t>(need, grid), 32 * kSplatWarps, 0, s>>>(P, sidx);
+        k_fw_splat<LPc><<<(unsigned)P.bstart[nk], kSplatThreads, 0, s>>>(P, sidx);
         DCRF_LAUNCHED();
         return DCRF_OK;
     }
