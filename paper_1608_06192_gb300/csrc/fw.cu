@@ -496,12 +496,13 @@ __global__ void k_fw_latupd(FwLat lt, int G, const double *alpha) {
 // One-hot splat S s of every lattice (App. B's one filter per iteration
 // starts from the splat of the vertex s): Sq[v][c] = sum over the incidences
 // (a, b) of vertex v with s_a = c of round(2^k b).  One block per run of
-// kSplatVerts consecutive vertices of one lattice: the block's threads stride
-// over the run's incidences (contiguous, grouped by vertex), find each one's
-// vertex by binary search in the run's offsets, and add into the block's
-// shared rows with integer atomics (exact, so the order does not matter);
-// the rows are then stored whole.  Every entry is written, so Sq needs no
-// clearing between iterations.
+// kSplatVerts consecutive vertices of one lattice, whose incidences are
+// contiguous (grouped by vertex).  Each thread takes a contiguous share of
+// them, so the lanes of a warp work on different vertices (few shared-memory
+// conflicts) and a thread's vertex only moves forward; it loads four
+// incidences and their s at a time, and adds into the block's shared rows
+// with integer atomics (exact, so the order does not matter).  The rows are
+// then stored whole: every entry is written, so Sq needs no clearing.
 struct SplatSet {
     const int32_t *off[DCRF_MAX_KERNELS];
     const int2 *inc[DCRF_MAX_KERNELS];
@@ -538,16 +539,29 @@ __global__ void __launch_bounds__(kSplatThreads) k_fw_splat(SplatSet P, const ui
     __syncthreads();
     const int e0 = soff[0], e1 = soff[nv];
     const float q = __ldg(qs);
-#pragma unroll 4
-    for (int e = e0 + threadIdx.x; e < e1; e += kSplatThreads) {
-        const int2 p = inc[e];
-        const unsigned c = s[p.x];
-        int lo = 0, hi = nv - 1;   // the last local vertex whose incidences start at or before e
+    const int chunk = (e1 - e0 + kSplatThreads - 1) / kSplatThreads;
+    const int tb = e0 + (int)threadIdx.x * chunk;
+    const int te = min(e1, tb + chunk);
+    if (tb < te) {
+        int lo = 0, hi = nv - 1;   // the last local vertex whose incidences start at or before tb
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (soff[mid] <= e) lo = mid; else hi = mid - 1;
+            if (soff[mid] <= tb) lo = mid; else hi = mid - 1;
         }
-        if (c < (unsigned)LP) atomicAdd(&rows[lo * LP + c], __float2uint_rn(q * __int_as_float(p.y)));
+        for (int e = tb; e < te; e += 4) {
+            int2 p[4];
+            unsigned c[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) p[k] = e + k < te ? inc[e + k] : make_int2(-1, 0);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) c[k] = p[k].x >= 0 ? (unsigned)s[p[k].x] : 0xFFu;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (e + k >= te) break;
+                while (soff[lo + 1] <= e + k) ++lo;
+                if (c[k] < (unsigned)LP) atomicAdd(&rows[lo * LP + c[k]], __float2uint_rn(q * __int_as_float(p[k].y)));
+            }
+        }
     }
     __syncthreads();
     uint32_t *dst = Sq + v0 * LP;
