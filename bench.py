@@ -307,23 +307,19 @@ def algorithmic_bytes(kind, n, L, lat_m, lat_d, storage):
     vertex id + weight per simplex corner (8 (d+1) per lattice).  Per lattice
     vertex row of Lp labels: the one-hot splat S s in 32-bit fixed point (4),
     B S s and the sliced B S y in the storage type (esz), Ylat and BY in float32.
-    The splat reads the incidences grouped by vertex (point + weight, 8 B per
-    simplex corner), s once, the vertex offsets, and writes its rows.
     """
     Lp = 8 if L <= 8 else (24 if L <= 24 else 64)
     esz = 2 if storage == "f16" else 4
     half_copy = 2 if storage == "f16" else 0
     if kind == "fw_pixel":
         per_px = 12 * L + 6 + sum(8 * (d + 1) for d in lat_d)
-        return n * per_px + sum(m * Lp * esz for m in lat_m)
-    if kind == "fw_splat":
-        return sum(n * (d + 1) * 8 + n + m * (4 * Lp + 4) for m, d in zip(lat_m, lat_d))
+        return n * per_px + sum(m * Lp * (esz + 4) for m in lat_m)
     if kind == "fw_blur":
         return sum(m * Lp * (4 + esz) + d * m * Lp * 2 * esz + (d + 1) * 8 * m for m, d in zip(lat_m, lat_d))
     if kind == "fw_latdot":
         return sum(m * Lp * (8 + esz) for m in lat_m)
     if kind == "fw_latupd":
-        return sum(m * Lp * (20 + esz + half_copy) + 4 * m for m in lat_m)
+        return sum(m * Lp * (24 + esz + half_copy) + 4 * m for m in lat_m)
     return 0
 
 
@@ -410,7 +406,7 @@ def main():
 
         # roofline of the dominant kernel (CUDA events on the launching stream)
         lat_m, lat_d = [lb.m, ls.m], [5, 2]
-        per_iter_launch = {"fw_pixel": 1, "fw_splat": 1, "fw_blur": max(lat_d) + 1, "fw_latdot": 2, "fw_latupd": 2}
+        per_iter_launch = {"fw_pixel": 1, "fw_blur": max(lat_d) + 1, "fw_latdot": 2, "fw_latupd": 2}
         roof = None
         kinds = {}
         for kind, (cnt, ms) in prof.items():

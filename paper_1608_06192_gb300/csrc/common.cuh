@@ -52,8 +52,6 @@ struct dcrf_lattice_s {
     int32_t *nbr = nullptr;          // [m][d+1][2]
     int32_t *vimg = nullptr;         // [m] image of each vertex
     float *ones = nullptr;           // [n] (K~_lattice 1)_a, s0 included
-    int32_t *inc_off = nullptr;      // [m+1] incidences of each vertex: inc[inc_off[v] .. inc_off[v+1])
-    int2 *inc = nullptr;             // [n(d+1)] (point, float bits of its barycentric weight), grouped by vertex
     int *status = nullptr;           // device status word (first error wins)
 };
 
@@ -129,7 +127,7 @@ enum ProfId {
     P_EMBED = 0, P_FINALIZE, P_NEIGHBOURS, P_SPLAT_DENSE, P_BLUR, P_SLICE,
     P_FW_PIXEL, P_FW_LATDOT, P_FW_ALPHA, P_FW_LATUPD, P_FW_LIN,
     P_LP_SORT, P_LP_RUNS, P_LP_SPLAT, P_LP_NEIGHBOURS, P_LP_BLUR, P_LP_SLICE, P_LP_COMBINE,
-    P_LP_PROJECT, P_LP_LOCAL, P_FW_BLUR, P_DCNEG_PIXEL, P_FW_SPLAT
+    P_LP_PROJECT, P_LP_LOCAL, P_FW_BLUR, P_DCNEG_PIXEL
 };
 struct ProfScope {
     ProfScope(int id, cudaStream_t s);

@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(1024) k_fw_alpha(PartSums P, double *alpha, dc
     }
 }
 
-// Ylat += alpha (Slat - Ylat); BY += alpha (BS - BY) (and its half copy).
+// Ylat += alpha (Slat - Ylat); BY += alpha (BS - BY) (and its half copy); Sq = 0.
 template <typename T>
 __global__ void k_fw_latupd(FwLat lt, int G, const double *alpha) {
     int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -491,81 +491,7 @@ __global__ void k_fw_latupd(FwLat lt, int G, const double *alpha) {
     st4(lt.Ylat, idx, y);
     st4(lt.BY, idx, by);
     if (lt.BYh) st4h(lt.BYh, idx, by);
-}
-
-// One-hot splat S s of every lattice (App. B's one filter per iteration
-// starts from the splat of the vertex s): Sq[v][c] = sum over the incidences
-// (a, b) of vertex v with s_a = c of round(2^k b).  One block per run of
-// kSplatVerts consecutive vertices of one lattice, whose incidences are
-// contiguous (grouped by vertex).  Each thread takes a contiguous share of
-// them, so the lanes of a warp work on different vertices (few shared-memory
-// conflicts) and a thread's vertex only moves forward; it loads four
-// incidences and their s at a time, and adds into the block's shared rows
-// with integer atomics (exact, so the order does not matter).  The rows are
-// then stored whole: every entry is written, so Sq needs no clearing.
-struct SplatSet {
-    const int32_t *off[DCRF_MAX_KERNELS];
-    const int2 *inc[DCRF_MAX_KERNELS];
-    uint32_t *Sq[DCRF_MAX_KERNELS];
-    const float *qs[DCRF_MAX_KERNELS];
-    int64_t m[DCRF_MAX_KERNELS];
-    int64_t bstart[DCRF_MAX_KERNELS + 1];   // prefix of the block counts
-    int nk;
-};
-constexpr int kSplatVerts = 128;
-constexpr int kSplatThreads = 256;
-
-template <int LP>
-__global__ void __launch_bounds__(kSplatThreads) k_fw_splat(SplatSet P, const uint8_t *__restrict__ s) {
-    __shared__ uint32_t rows[kSplatVerts * LP];
-    __shared__ int32_t soff[kSplatVerts + 1];
-    const int64_t blk = blockIdx.x;
-    int mm = 0;
-#pragma unroll
-    for (int k = 1; k < DCRF_MAX_KERNELS; ++k)
-        if (k < P.nk && blk >= P.bstart[k]) mm = k;
-    const int32_t *off = P.off[0];
-    const int2 *inc = P.inc[0];
-    uint32_t *Sq = P.Sq[0];
-    const float *qs = P.qs[0];
-    int64_t m = P.m[0];
-#pragma unroll
-    for (int k = 1; k < DCRF_MAX_KERNELS; ++k)
-        if (k == mm) { off = P.off[k]; inc = P.inc[k]; Sq = P.Sq[k]; qs = P.qs[k]; m = P.m[k]; }
-    const int64_t v0 = (blk - P.bstart[mm]) * kSplatVerts;
-    const int nv = (int)min((int64_t)kSplatVerts, m - v0);
-    for (int i = threadIdx.x; i <= nv; i += kSplatThreads) soff[i] = off[v0 + i];
-    for (int i = threadIdx.x; i < nv * LP; i += kSplatThreads) rows[i] = 0u;
-    __syncthreads();
-    const int e0 = soff[0], e1 = soff[nv];
-    const float q = __ldg(qs);
-    const int chunk = (e1 - e0 + kSplatThreads - 1) / kSplatThreads;
-    const int tb = e0 + (int)threadIdx.x * chunk;
-    const int te = min(e1, tb + chunk);
-    if (tb < te) {
-        int lo = 0, hi = nv - 1;   // the last local vertex whose incidences start at or before tb
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (soff[mid] <= tb) lo = mid; else hi = mid - 1;
-        }
-        for (int e = tb; e < te; e += 4) {
-            int2 p[4];
-            unsigned c[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) p[k] = e + k < te ? inc[e + k] : make_int2(-1, 0);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) c[k] = p[k].x >= 0 ? (unsigned)s[p[k].x] : 0xFFu;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (e + k >= te) break;
-                while (soff[lo + 1] <= e + k) ++lo;
-                if (c[k] < (unsigned)LP) atomicAdd(&rows[lo * LP + c[k]], __float2uint_rn(q * __int_as_float(p[k].y)));
-            }
-        }
-    }
-    __syncthreads();
-    uint32_t *dst = Sq + v0 * LP;
-    for (int i = threadIdx.x; i < nv * LP; i += kSplatThreads) dst[i] = rows[i];
+    reinterpret_cast<uint4 *>(lt.Sq)[idx] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 // Decision trace: row *counter of trace (when below rows) receives s, the
@@ -767,8 +693,6 @@ struct Solver {
             l.pvid = lat->pvid;
             l.pbary = lat->pbary;
             l.vimg = lat->vimg;
-            l.inc_off = lat->inc_off;
-            l.inc = lat->inc;
             l.m = lat->m;
             l.d1 = lat->d + 1;
             l.ws0 = (float)(weights[m] * lat->s0);
@@ -1054,40 +978,12 @@ struct Solver {
         return pixel_t<64, T, POT>(Y, phi, start);
     }
 
-    // The one-hot splat of s into Sq for every lattice (after a pixel pass).
-    template <int LPc>
-    dcrf_status splat_t() {
-        SplatSet P{};
-        P.nk = nk;
-        P.bstart[0] = 0;
-        for (int m = 0; m < nk; ++m) {
-            P.off[m] = F.l[m].inc_off;
-            P.inc[m] = F.l[m].inc;
-            P.Sq[m] = F.l[m].Sq;
-            P.qs[m] = F.l[m].qs;
-            P.m[m] = F.l[m].m;
-            P.bstart[m + 1] = P.bstart[m] + (F.l[m].m + kSplatVerts - 1) / kSplatVerts;
-        }
-        if (P.bstart[nk] == 0) return DCRF_OK;
-        ProfScope ps(P_FW_SPLAT, s);
-        k_fw_splat<LPc><<<(unsigned)P.bstart[nk], kSplatThreads, 0, s>>>(P, sidx);
-        DCRF_LAUNCHED();
-        return DCRF_OK;
-    }
-
-    dcrf_status splat() {
-        if (Lp == 8) return splat_t<8>();
-        if (Lp == 24) return splat_t<24>();
-        return splat_t<64>();
-    }
-
     dcrf_status pixel(float *Y, const float *phi, bool start) {
         dcrf_status st;
         if (storage == DCRF_STORAGE_F16)
             st = potts ? pixel_lp<__half, true>(Y, phi, start) : pixel_lp<__half, false>(Y, phi, start);
         else
             st = potts ? pixel_lp<float, true>(Y, phi, start) : pixel_lp<float, false>(Y, phi, start);
-        if (st == DCRF_OK && n > 0) st = splat();
         if (st != DCRF_OK || !trace || n == 0) return st;
         k_fw_trace<<<(unsigned)std::min<int64_t>(nblocks(n, 256), 4096), 256, 0, s>>>(sidx, trace, counter, n,
                                                                                       trace_rows);

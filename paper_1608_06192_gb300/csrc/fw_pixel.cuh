@@ -12,9 +12,8 @@ namespace {
 // Pixel-kernel modes: kFix gathers the corner rows of the common two-kernel
 // case (bilateral d = 5, spatial d = 2) with every index loaded up front;
 // kF2 accumulates the gathered rows with packed two-wide FP32 FMAs.  (A
-// shared-memory hash aggregation of the one-hot splat was measured 2x slower
-// than plain reductions in L2: many pixels of a block hit the same key; the
-// splat is now a separate vertex-side gather, k_fw_splat.)
+// shared-memory hash aggregation of the splat was measured 2x slower than
+// plain FP32 reductions in L2: many pixels of a block hit the same key.)
 // kL3 is the label-split layout (three lanes per pixel, 80 pixels per block,
 // see pixel3); kEarly gathers the corner rows while the chunk's y and lin
 // rows are still in flight to shared memory.
@@ -50,8 +49,6 @@ struct FwLat {
     __half *BYh;     // [m][Lp] half copy of BY sliced by the pixel kernel (half storage only)
     uint32_t *Sq;    // [m][Lp] S s in fixed point: value = Sq * qs[1] (integer sums: deterministic)
     const float *qs; // {2^k, 2^-k} of this lattice's fixed point
-    const int32_t *inc_off;   // [m+1] incidences of each vertex (the lattice's)
-    const int2 *inc;          // (point, weight bits), grouped by vertex
     void *BS;        // [m][Lp] B S s (float or half)
     void *tmp;       // blur scratch (same type as BS)
 };
@@ -116,8 +113,9 @@ __device__ __forceinline__ void block_reduce_add(double (&v)[N], double *acc) {
 //   4: -sum_w <y', mu e_s'> + y'(s') d(s')   (pixel part of <y', (Psi+D) s'>)
 //   5: -sum_w mu(s', s') + d(s')            (pixel part of <s', (Psi+D) s'>)
 //   6: <y', D y'>  7: <phi, y'> (only when phi is given)
-// and s' is stored; the splat S s' is formed afterwards by k_fw_splat,
-// which gathers over every vertex's incidences.
+// and S s' is splatted into Sq: every corner adds its barycentric weight
+// rounded to a multiple of 2^-k (integer reductions in L2, so the sums and
+// everything after them do not depend on the order of the atomics).
 struct PixArgs {
     const Chunk *chunks;
     const double *alpha;   // [batch] or null (start: alpha = 0)
@@ -356,7 +354,7 @@ __device__ __forceinline__ void gather_pair(const FwLat &la, const FwLat &lb, in
 // One chunk: every pixel of it (see the comment above PixArgs).
 // Returns false (for the whole block) when the chunk's tile copy did not
 // complete within both bounded waits: DCRF_E_TIMEOUT is then flagged, the
-// block touches neither the tile nor y and s, and the launch's
+// block touches neither the tile nor y, s and the splat, and the launch's
 // outputs are invalid.
 template <int LP, typename TB, bool POTTS, int MODE>
 __device__ __forceinline__ bool pixel_chunk(const PixArgs &A, const FwLats &F, const Chunk &ch, float *sy,
@@ -559,6 +557,19 @@ __device__ __forceinline__ bool pixel_chunk(const PixArgs &A, const FwLats &F, c
         }
       }
         A.s[a] = (uint8_t)sb;
+        // splat of the one-hot s' into Sq (integer reductions in L2).  A delta
+        // update (+b at s', -b at s) does not pay: along the Frank-Wolfe path
+        // almost every pixel's argmin moves at every iteration.
+#pragma unroll
+        for (int mm = 0; mm < DCRF_MAX_KERNELS; ++mm) {
+            if (mm >= F.nk) break;
+            const FwLat &lt = F.l[mm];
+            const float q = __ldg(lt.qs);
+            for (int k = 0; k < lt.d1; ++k) {
+                const int v = __ldg(lt.pvid + a * lt.d1 + k);
+                if (v >= 0) atomicAdd(lt.Sq + (int64_t)v * LP + sb, __float2uint_rn(q * __ldg(lt.pbary + a * lt.d1 + k)));
+            }
+        }
     }
     return true;
 }
@@ -567,7 +578,7 @@ __device__ __forceinline__ bool pixel_chunk(const PixArgs &A, const FwLats &F, c
 // pixel, lane q of a pixel owns labels 8q .. 8q+7, so one warp instruction
 // gathers ten whole 48-byte (FP16) corner rows instead of one 16-byte piece
 // of 32 different rows.  Lanes 30 and 31 of each warp are idle; a warp holds
-// ten pixels.  Same sums as pixel_chunk: the per-pixel scalars
+// ten pixels.  Same sums and splat as pixel_chunk: the per-pixel scalars
 // (total over labels, argmin) are combined over the three lanes in a fixed
 // order, so the lanes of a pixel agree bit for bit.
 constexpr int kL3Warps = 8;                 // warps per block
@@ -712,6 +723,18 @@ __device__ __forceinline__ void pixel3(const PixArgs &A, const FwLats &F, const 
             part[5] = dpot;                                  // mu(s', s') = 0
         }
         if (q == 0) A.s[a] = (uint8_t)sbw;
+        // splat of the one-hot s': lane q takes corners k = q, q + 3, ...
+#pragma unroll
+        for (int mm = 0; mm < DCRF_MAX_KERNELS; ++mm) {
+            if (mm >= F.nk) break;
+            const FwLat &lt = F.l[mm];
+            const float qk = __ldg(lt.qs);
+            for (int k = q; k < lt.d1; k += 3) {
+                const int v = __ldg(lt.pvid + a * lt.d1 + k);
+                if (v >= 0)
+                    atomicAdd(lt.Sq + (int64_t)v * LP + sbw, __float2uint_rn(qk * __ldg(lt.pbary + a * lt.d1 + k)));
+            }
+        }
     }
 }
 

@@ -586,29 +586,8 @@ static void lattice_free(dcrf_lattice lat) {
     cudaFree(lat->nbr);
     cudaFree(lat->vimg);
     cudaFree(lat->ones);
-    cudaFree(lat->inc_off);
-    cudaFree(lat->inc);
     cudaFree(lat->status);
     delete lat;
-}
-
-// Incidences grouped by vertex: the corners of every point counted per vertex,
-// offsets by a scan, then every corner placed in its vertex's range (in any
-// order: the sums over a vertex's incidences are integer sums).
-__global__ void k_inc_count(const int32_t *__restrict__ pvid, int64_t cnt, int32_t *__restrict__ deg) {
-    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= cnt) return;
-    const int v = pvid[e];
-    if (v >= 0) atomicAdd(deg + v, 1);
-}
-__global__ void k_inc_fill(const int32_t *__restrict__ pvid, const float *__restrict__ pbary, int64_t cnt, int d1,
-                           const int32_t *__restrict__ off, int32_t *__restrict__ cursor, int2 *__restrict__ inc) {
-    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= cnt) return;
-    const int v = pvid[e];
-    if (v < 0) return;
-    const int pos = off[v] + atomicAdd(cursor + v, 1);
-    inc[pos] = make_int2((int)(e / d1), __float_as_int(pbary[e]));
 }
 
 __global__ void k_fill(float *p, float v, int64_t n) {
@@ -759,29 +738,6 @@ static dcrf_status build_typed(dcrf_lattice lat, const float *feat, cudaStream_t
         k_neighbours<D><<<blocks_for(m, 128), 128, 0, s>>>(lat->keys, lat->vimg, m, table, ids, base_d, mask_d,
                                                            lat->nbr);
         DCRF_LAUNCHED();
-    }
-    // incidences grouped by vertex (the one-hot splat of the Frank-Wolfe
-    // solver gathers over them)
-    DCRF_TRY(cudaMalloc(&lat->inc_off, (m + 1) * sizeof(int32_t)));
-    DCRF_TRY(cudaMalloc(&lat->inc, (n > 0 ? n : 1) * D1 * sizeof(int2)));
-    if (n > 0 && m > 0) {
-        int32_t *deg, *cursor;
-        DCRF_CHECK_STATUS(sc.get(&deg, (size_t)m + 1));
-        DCRF_CHECK_STATUS(sc.get(&cursor, (size_t)m));
-        DCRF_TRY(cudaMemsetAsync(deg, 0, (m + 1) * sizeof(int32_t), s));
-        DCRF_TRY(cudaMemsetAsync(cursor, 0, m * sizeof(int32_t), s));
-        k_inc_count<<<blocks_for(n * D1, 256), 256, 0, s>>>(lat->pvid, n * D1, deg);
-        DCRF_LAUNCHED();
-        size_t ib = 0;
-        DCRF_TRY(cub::DeviceScan::ExclusiveSum(nullptr, ib, deg, lat->inc_off, (int)(m + 1), s));
-        char *it;
-        DCRF_CHECK_STATUS(sc.get(&it, ib));
-        DCRF_TRY(cub::DeviceScan::ExclusiveSum(it, ib, deg, lat->inc_off, (int)(m + 1), s));
-        k_inc_fill<<<blocks_for(n * D1, 256), 256, 0, s>>>(lat->pvid, lat->pbary, n * D1, D1, lat->inc_off, cursor,
-                                                           lat->inc);
-        DCRF_LAUNCHED();
-    } else {
-        DCRF_TRY(cudaMemsetAsync(lat->inc_off, 0, (m + 1) * sizeof(int32_t), s));
     }
     // K~ 1 for the d vector of Eq. 11; S 1 is summed in 64-bit fixed point
     // (integer sums: the same lattice comes out of every build of the same

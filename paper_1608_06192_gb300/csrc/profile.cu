@@ -26,7 +26,7 @@ std::vector<cudaEvent_t> g_pool;
 const char *kNames[] = {"embed_insert", "lattice_finalize", "neighbours", "splat_dense", "blur_pass", "slice",
                         "fw_pixel", "fw_latdot", "fw_alpha", "fw_latupd", "fw_lin", "lp_sort",
                         "lp_runs", "lp_splat", "lp_neighbours", "lp_blur", "lp_slice", "lp_combine",
-                        "lp_project", "lp_local", "fw_blur", "dcneg_pixel", "fw_splat"};
+                        "lp_project", "lp_local", "fw_blur", "dcneg_pixel"};
 constexpr int kNumNames = sizeof(kNames) / sizeof(kNames[0]);
 
 cudaEvent_t get_event() {
