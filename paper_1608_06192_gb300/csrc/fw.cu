@@ -900,6 +900,9 @@ struct Solver {
                 DCRF_PIX_CASE(13);
                 DCRF_PIX_CASE(14);
                 DCRF_PIX_CASE(15);
+                DCRF_PIX_CASE(16);
+                DCRF_PIX_CASE(17);
+                DCRF_PIX_CASE(18);
             default: return pixel_v<LPc, T, POT, kPixPB[0], kPixMB[0], kPixMode[0]>(Y, phi, start, al);
             }
 #undef DCRF_PIX_CASE
@@ -917,14 +920,14 @@ struct Solver {
     dcrf_status tune(const float *Y) {
         if (const char *force = std::getenv("DCRF_PIXEL_VARIANT")) {   // testing hook
             const int v = std::atoi(force);
-            variant = (LPc == 24 && POT && v >= 0 && v < kPixVariants) ? v : 0;
+            variant = (LPc == 24 && POT && v >= 0 && v < kPixVariants && pixel_variant_fits(v, L)) ? v : 0;
             return DCRF_OK;
         }
         static std::mutex mu_;
-        static std::map<std::tuple<int, int, bool, int>, int> cache;
+        static std::map<std::tuple<int, int, int, bool, int>, int> cache;
         int bucket = 0;
         while ((int64_t)1 << (bucket + 1) <= n) ++bucket;
-        const auto key = std::make_tuple(LPc, storage, POT, bucket);
+        const auto key = std::make_tuple(LPc, L, storage, POT, bucket);
         {
             std::lock_guard<std::mutex> lk(mu_);
             auto it = cache.find(key);
@@ -943,6 +946,7 @@ struct Solver {
         int arg = 0;
         float *Yw = const_cast<float *>(Y);
         for (int v = 0; v < kPixVariants; ++v) {
+            if (!pixel_variant_fits(v, L)) continue;
             DCRF_CHECK_STATUS((pixel_var<LPc, T, POT>(v, Yw, nullptr, false, zero)));   // warm-up
             DCRF_TRY(cudaEventRecord(e0, s));
             for (int r = 0; r < 3; ++r) DCRF_CHECK_STATUS((pixel_var<LPc, T, POT>(v, Yw, nullptr, false, zero)));

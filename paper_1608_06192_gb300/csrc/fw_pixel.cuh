@@ -21,16 +21,25 @@ namespace {
 // completed on an mbarrier, where the rows are 16-byte aligned.
 // kLean (Potts) computes y' and the label totals in one pass and tracks only
 // the argmin, its gradient and X(s') in the label loop.
-constexpr int kFix = 1, kF2 = 2, kL3 = 4, kEarly = 8, kBulk = 16, kLean = 32;
-constexpr int kPixVariants = 16;
-constexpr int kPixPB[kPixVariants] = {256, 128, 256, 128, 256, 80, 128, 256, 128, 128, 128, 128, 128, 128, 128, 128};
-constexpr int kPixMB[kPixVariants] = {4, 8, 3, 6, 3, 0, 6, 3, 6, 8, 7, 8, 7, 6, 7, 8};
+// kL21 fixes L = 21 at compile time (the label count of the segmentation
+// workloads): the loops over the padded 24 labels lose their runtime bounds
+// and the padding labels' accumulators and FMAs go away.
+constexpr int kFix = 1, kF2 = 2, kL3 = 4, kEarly = 8, kBulk = 16, kLean = 32, kL21 = 64;
+constexpr int kPixVariants = 19;
+constexpr int kPixPB[kPixVariants] = {256, 128, 256, 128, 256, 80, 128, 256, 128, 128,
+                                      128, 128, 128, 128, 128, 128, 128, 128, 128};
+constexpr int kPixMB[kPixVariants] = {4, 8, 3, 6, 3, 0, 6, 3, 6, 8, 7, 8, 7, 6, 7, 8, 7, 8, 6};
 constexpr int kPixMode[kPixVariants] = {0,           0,           kFix,         kFix,
                                         kFix | kF2,  kL3,         kFix | kEarly, kFix | kEarly,
                                         kFix | kF2 | kEarly, kFix | kEarly, kFix | kF2 | kEarly,
                                         kFix | kF2 | kEarly, kFix | kF2 | kEarly | kBulk,
                                         kFix | kF2 | kEarly | kBulk, kFix | kF2 | kEarly | kBulk | kLean,
-                                        kFix | kF2 | kEarly | kBulk | kLean};
+                                        kFix | kF2 | kEarly | kBulk | kLean,
+                                        kFix | kF2 | kEarly | kBulk | kLean | kL21,
+                                        kFix | kF2 | kEarly | kBulk | kLean | kL21,
+                                        kFix | kF2 | kEarly | kBulk | kLean | kL21};
+// whether variant v can run a problem with L labels
+constexpr bool pixel_variant_fits(int v, int L) { return (kPixMode[v] & kL21) == 0 || L == 21; }
 // chunk list of a pixel-block size (256, 128 or 80 pixels)
 constexpr int chunk_list(int pb) { return pb == 256 ? 0 : (pb == 128 ? 1 : 2); }
 constexpr int chunk_warps(int list) { return list == 0 ? 8 : (list == 1 ? 4 : 8); }
@@ -359,7 +368,7 @@ __device__ __forceinline__ void gather_pair(const FwLat &la, const FwLat &lb, in
 template <int LP, typename TB, bool POTTS, int MODE>
 __device__ __forceinline__ bool pixel_chunk(const PixArgs &A, const FwLats &F, const Chunk &ch, float *sy,
                                             const float *sl, float (&part)[NS], unsigned long long *tbar) {
-    const int L = A.L;
+    const int L = (MODE & kL21) ? 21 : A.L;
     const bool start = A.alpha == nullptr;
     const float al = start ? 0.f : (float)A.alpha[ch.image];
 #pragma unroll

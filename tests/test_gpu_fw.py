@@ -132,11 +132,12 @@ def test_fw_graph_path_matches_eager(dcrf):
     np.testing.assert_array_equal(Y1.cpu().numpy(), Y2.cpu().numpy())
 
 
-@pytest.mark.parametrize("variant", range(16))
+@pytest.mark.parametrize("variant", range(19))
 def test_fw_every_pixel_variant(dcrf, variant, monkeypatch):
     # the autotuner chooses among these layouts of the pixel pass (block
     # shapes, index prefetch, packed FMAs, three lanes per pixel, gather
-    # during the tile copy, bulk tile copies); each must follow the oracle
+    # during the tile copy, bulk tile copies, the label count fixed at 21);
+    # each must follow the oracle
     monkeypatch.setenv("DCRF_PIXEL_VARIANT", str(variant))
     p = S.make_problem(96, 64, 8, 21, seed=13)
     for storage in ("f32", "f16"):
@@ -144,7 +145,7 @@ def test_fw_every_pixel_variant(dcrf, variant, monkeypatch):
         _check_against_oracle([p], g, Y, rec, 15, mono=1e-6 if storage == "f32" else 1e-4)
 
 
-@pytest.mark.parametrize("variant", [12, 13, 14, 15])
+@pytest.mark.parametrize("variant", [12, 13, 14, 15, 16])
 def test_fw_bulk_variant_on_unaligned_batch(dcrf, variant, monkeypatch):
     # chunks whose rows do not start or end on 16 bytes fall back to cp.async
     # (image 0 ends after 851 pixels: 851 x 21 floats is not a multiple of 4)
@@ -182,3 +183,12 @@ def test_fw_persistent_blur_strides_over_many_rows(dcrf, monkeypatch):
         _, _, rec_o = qp.frank_wolfe(c, probs[b].y0, iters)
         scale = np.abs(rec_o[:, 0]).max()
         assert np.abs(rec[:, b, 0] - rec_o[:, 0]).max() <= 1e-3 * scale
+
+
+def test_fw_fixed_label_count_variant_falls_back(dcrf, monkeypatch):
+    # the variants compiled for L = 21 are never used for another label count:
+    # forcing one with L = 5 runs the generic layout
+    monkeypatch.setenv("DCRF_PIXEL_VARIANT", "16")
+    p = S.qp_small()
+    g, Y, rec = _run_fw(dcrf, [p], 20)
+    _check_against_oracle([p], g, Y, rec, 20)
