@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-cpu-all-cores", action="store_true")
     ap.add_argument("--no-lp", action="store_true")
     ap.add_argument("--no-uneven", action="store_true", help="skip the uneven-size batch arm")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the batched other-storage and single-image FP16 arms")
     ap.add_argument("--no-dcneg", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the CCCP and reverse-mode timings")
     return ap.parse_args()
@@ -474,14 +476,16 @@ def main():
         single32 = arm([l1b, l1s], phi[:n1], y0[:n1], "f32", 1, 5)
         plain_fp32 = single32["value"]
         other = "f32" if args.storage == "f16" else "f16"
-        precision = {
-            "note": "lattice storage at equal batching: the batched arms run the headline batch, the single "
-                    "arms its first image alone",
-            f"batched_{args.storage}": {"value": value, "unit": UNIT, "ms_per_step": round(ms_step, 3)},
-            f"batched_{other}": arm([lb, ls], phi, y0, other, B, 3),
-            "single_image_f32": single32,
-            "single_image_f16": arm([l1b, l1s], phi[:n1], y0[:n1], "f16", 1, 5),
-        }
+        precision = None
+        if not args.no_precision:
+            precision = {
+                "note": "lattice storage at equal batching: the batched arms run the headline batch, the single "
+                        "arms its first image alone",
+                f"batched_{args.storage}": {"value": value, "unit": UNIT, "ms_per_step": round(ms_step, 3)},
+                f"batched_{other}": arm([lb, ls], phi, y0, other, B, 3),
+                "single_image_f32": single32,
+                "single_image_f16": arm([l1b, l1s], phi[:n1], y0[:n1], "f16", 1, 5),
+            }
         # the uneven batch: 32 images of W ~ U[240,500] x H ~ U[160,500]
         uneven = None
         if not args.no_uneven:
