@@ -42,6 +42,7 @@ struct dcrf_lattice_s {
     int64_t m = 0;
     int batch = 0;
     double s0 = 1.0;                 // output scale of the slice
+    double s1max = 0.0;              // max over vertices of (S 1)_v, the summed barycentric weights
     std::vector<int64_t> point_off;  // host [batch+1]
     std::vector<int64_t> vert_off;   // host [batch+1]
     int64_t *point_off_d = nullptr;  // device [batch+1]

@@ -505,31 +505,6 @@ __global__ void k_fw_trace(const uint8_t *__restrict__ s, uint8_t *__restrict__ 
         dst[i] = s[i];
 }
 
-// Fixed point of the one-hot splat.  An entry of S s is a sum of barycentric
-// weights of the corners at that vertex, at most (S 1)_v; k_fw_s1 forms S 1
-// (float atomics: only a bound is needed), k_fw_qmax its maximum, and
-// k_fw_qscale the largest 2^k <= 2^30 with 2^k (1.001 max (S 1) + 1) <= 2^31,
-// so that the integer sums of the rounded weights cannot overflow.
-__global__ void k_fw_s1(const int32_t *__restrict__ pvid, const float *__restrict__ pbary, int64_t cnt, float *acc) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= cnt) return;
-    const int v = pvid[i];
-    if (v >= 0) atomicAdd(acc + v, pbary[i]);
-}
-__global__ void k_fw_qmax(const float *__restrict__ acc, int64_t m, unsigned *qmax) {
-    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const float x = v < m ? fmaxf(acc[v], 0.f) : 0.f;
-    const unsigned u = __reduce_max_sync(0xffffffffu, __float_as_uint(x));   // non-negative floats order as integers
-    if ((threadIdx.x & 31) == 0) atomicMax(qmax, u);
-}
-__global__ void k_fw_qscale(const unsigned *qmax, float *qs) {
-    const float b = 1.001f * __uint_as_float(*qmax) + 1.f;
-    int k = 30;
-    while (k > 0 && ldexpf(b, k) > 2147483648.f) --k;
-    qs[0] = ldexpf(1.f, k);
-    qs[1] = ldexpf(1.f, -k);
-}
-
 // y^0 must lie on the simplex (rows non-negative, summing to one within
 // 1e-5); a row that does not is reported as DCRF_E_INVAL.
 __global__ void k_fw_check_y(const float *__restrict__ Y, int64_t n, int L, int *status) {
@@ -768,30 +743,21 @@ struct Solver {
             k_fw_lin<<<nblocks(n * L, 256), 256, 0, s>>>(n, L, unaries, c, musum, nullptr, 1.f, lin, status);
             DCRF_LAUNCHED();
         }
-        // fixed-point scales of the one-hot splats (the blur scratch tmp,
-        // at least m floats, holds S 1)
+        // fixed-point scales of the one-hot splats: an entry of S s is at most
+        // (S 1)_v <= s1max (a bound from the lattice build), so with
+        // 2^k (1.001 s1max + 1) <= 2^31 the integer sums cannot overflow
         float *qs_all;
-        unsigned *qmax_all;
         DCRF_CHECK_STATUS(sc.get(&qs_all, (size_t)2 * nk));
-        DCRF_CHECK_STATUS(sc.get(&qmax_all, (size_t)nk));
-        DCRF_TRY(cudaMemsetAsync(qmax_all, 0, nk * sizeof(unsigned), s));
+        std::vector<float> qs_h(2 * nk);
         for (int m = 0; m < nk; ++m) {
-            FwLat &l = F.l[m];
-            l.qs = qs_all + 2 * m;
-            float *acc = reinterpret_cast<float *>(l.tmp);
-            if (l.m > 0) {
-                DCRF_TRY(cudaMemsetAsync(acc, 0, l.m * sizeof(float), s));
-                const int64_t cnt = n * l.d1;
-                if (cnt > 0) {
-                    k_fw_s1<<<nblocks(cnt, 256), 256, 0, s>>>(l.pvid, l.pbary, cnt, acc);
-                    DCRF_LAUNCHED();
-                }
-                k_fw_qmax<<<nblocks(l.m, 256), 256, 0, s>>>(acc, l.m, qmax_all + m);
-                DCRF_LAUNCHED();
-            }
-            k_fw_qscale<<<1, 1, 0, s>>>(qmax_all + m, qs_all + 2 * m);
-            DCRF_LAUNCHED();
+            const double b = 1.001 * lattices[m]->s1max + 1.0;
+            int k = 30;
+            while (k > 0 && std::ldexp(b, k) > 2147483648.0) --k;
+            qs_h[2 * m] = std::ldexp(1.f, k);
+            qs_h[2 * m + 1] = std::ldexp(1.f, -k);
+            F.l[m].qs = qs_all + 2 * m;
         }
+        DCRF_TRY(cudaMemcpyAsync(qs_all, qs_h.data(), 2 * nk * sizeof(float), cudaMemcpyHostToDevice, s));
         // Ylat = S y0 (fixed point, then float32), BY = B S y0
         if (n > 0) {
             k_fw_check_y<<<nblocks(n, 256), 256, 0, s>>>(Y, n, L, status);

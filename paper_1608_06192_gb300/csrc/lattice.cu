@@ -459,9 +459,13 @@ __global__ void k_splat_ones_q(const int32_t *__restrict__ pvid, const float *__
     const int v = pvid[i];
     if (v >= 0) atomicAdd(acc + v, (unsigned long long)__double2ull_rn(ldexp((double)pbary[i], 32)));
 }
-__global__ void k_ones_rows(const unsigned long long *__restrict__ acc, int64_t m, float *V) {
+__global__ void k_ones_rows(const unsigned long long *__restrict__ acc, int64_t m, float *V,
+                            unsigned long long *amax) {
     const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (v < m) reinterpret_cast<float4 *>(V)[v] = make_float4((float)ldexp((double)acc[v], -32), 0.f, 0.f, 0.f);
+    const unsigned long long a = v < m ? acc[v] : 0ull;
+    if (v < m) reinterpret_cast<float4 *>(V)[v] = make_float4((float)ldexp((double)a, -32), 0.f, 0.f, 0.f);
+    const unsigned long long wmax = __reduce_max_sync(0xffffffffu, (unsigned)(a >> 32)) + 1ull;   // upper bound
+    if ((threadIdx.x & 31) == 0) atomicMax(amax, wmax);
 }
 
 // Dense splat: V[vertex_k(a)][c] += b_k(a) * Y[a][c]; one thread per (point,
@@ -739,6 +743,7 @@ static dcrf_status build_typed(dcrf_lattice lat, const float *feat, cudaStream_t
                                                            lat->nbr);
         DCRF_LAUNCHED();
     }
+    unsigned long long s1bound = 0;
     // K~ 1 for the d vector of Eq. 11; S 1 is summed in 64-bit fixed point
     // (integer sums: the same lattice comes out of every build of the same
     // points, bit for bit)
@@ -748,12 +753,14 @@ static dcrf_status build_typed(dcrf_lattice lat, const float *feat, cudaStream_t
         DCRF_CHECK_STATUS(sc.get(&V, (size_t)m * 4));
         DCRF_CHECK_STATUS(sc.get(&A, (size_t)m * 4));
         DCRF_CHECK_STATUS(sc.get(&B, (size_t)m * 4));
-        DCRF_CHECK_STATUS(sc.get(&acc, (size_t)m));
-        DCRF_TRY(cudaMemsetAsync(acc, 0, (size_t)m * sizeof(unsigned long long), s));
+        DCRF_CHECK_STATUS(sc.get(&acc, (size_t)m + 1));
+        DCRF_TRY(cudaMemsetAsync(acc, 0, (size_t)(m + 1) * sizeof(unsigned long long), s));
         k_splat_ones_q<<<blocks_for(n * D1, 256), 256, 0, s>>>(lat->pvid, lat->pbary, n * D1, acc);
         DCRF_LAUNCHED();
-        k_ones_rows<<<blocks_for(m, 256), 256, 0, s>>>(acc, m, V);
+        // acc[m]: an integer upper bound of max_v (S 1)_v (read at the sync below)
+        k_ones_rows<<<blocks_for(m, 256), 256, 0, s>>>(acc, m, V, acc + m);
         DCRF_LAUNCHED();
+        DCRF_TRY(cudaMemcpyAsync(&s1bound, acc + m, sizeof(s1bound), cudaMemcpyDeviceToHost, s));
         DCRF_CHECK_STATUS(dcrf_blur(lat, V, A, B, 4, DCRF_STORAGE_F32, false, s));
         k_slice<float><<<blocks_for(n, 256), 256, 0, s>>>(A, n, 1, 1, D1, lat->pvid, lat->pbary, (float)lat->s0,
                                                           lat->ones);
@@ -763,6 +770,7 @@ static dcrf_status build_typed(dcrf_lattice lat, const float *feat, cudaStream_t
     DCRF_TRY(cudaMemcpyAsync(&hstatus, lat->status, sizeof(int), cudaMemcpyDeviceToHost, s));
     DCRF_TRY(cudaStreamSynchronize(s));
     if (hstatus != 0) return (dcrf_status)hstatus;
+    lat->s1max = (double)s1bound;
     return DCRF_OK;
 }
 
