@@ -121,6 +121,25 @@ dcrf_status dcrf_lattice_export(dcrf_lattice lat, int32_t *keys, int32_t *point_
                                 float *point_weight, int32_t *neighbours, dcrf_stream stream);
 
 /*
+ * Check mode for the tables the kernels index with (no counterpart in the
+ * paper).  point_vertex [n][d+1] int32, point_weight [n][d+1] float32 and
+ * neighbours [m][d+1][2] int32 are device arrays laid out as
+ * dcrf_lattice_export writes them; point_offsets and vertex_offsets are host
+ * [batch+1] (points and vertices of each image).  A table passes when every
+ * corner's vertex is -1 or a vertex of the point's own image, every weight is
+ * finite in [0, 1] and each point's weights sum to one within 1e-5, and every
+ * blur neighbour is -1 or a vertex of the same image.  Synchronises; returns
+ * DCRF_E_INVAL when an entry fails (bad_entries, host, may be NULL, receives
+ * how many) or when the sizes disagree.  dcrf_lattice_validate runs it on a
+ * lattice's own tables.
+ */
+dcrf_status dcrf_check_lattice_tables(const int32_t *point_vertex, const float *point_weight, int64_t n, int d,
+                                      const int32_t *neighbours, int64_t m, const int64_t *point_offsets,
+                                      const int64_t *vertex_offsets, int batch, int64_t *bad_entries,
+                                      dcrf_stream stream);
+dcrf_status dcrf_lattice_validate(dcrf_lattice lat, int64_t *bad_entries, dcrf_stream stream);
+
+/*
  * Eq. 6 through the lattice: out = K~ Y, K~ = s0 S^T B_d ... B_0 S, i.e.
  * splat, d+1 axis blurs [1/4, 1/2, 1/4] (axis order 0..d), slice; not
  * normalised (Appendix A).  Y, out: device [N][L] float32 (out may not alias
@@ -162,6 +181,9 @@ dcrf_status dcrf_filter_adjoint(dcrf_lattice lat, const float *U, int L, float *
  *   same points and batch; weights: host [n_kernels] w_m >= 0.
  * compat: host [L][L] label compatibility mu, or NULL for Potts [i != j].
  * Y: device [N][L]; on entry y^0 (rows on the simplex), on exit y^iters.
+ * The rows of y^0 are checked on the device (non-negative, summing to one
+ * within 1e-5); a row that is not is reported as DCRF_E_INVAL in the status
+ * word, returned here when records are asked for.
  * records: host [iters][batch] or NULL; when given, the call synchronises.
  * Pairwise operator: Psi = mu (x) (sum_m w_m K~_m - (sum_m w_m) I) (Eq. 7),
  * d_a(i) = (sum_j |mu_ij|) max(0, (K~1)_a - sum_m w_m) (Eq. 11).

@@ -71,6 +71,8 @@ _SIGS = {
     "dcrf_round_kt": ([_P, _I64, _I, _I, _P, _P, _I, _P, _P, _P], _I),
     "dcrf_simplex_project": ([_P, _I64, _I, _P, _P], _I),
     "dcrf_selftest_bounded_wait": ([_P, _I64, _I, _P], _I),
+    "dcrf_check_lattice_tables": ([_P, _P, _I64, _I, _P, _I64, _P, _P, _I, _P, _P], _I),
+    "dcrf_lattice_validate": ([_P, _P, _P], _I),
     "dcrf_profile_enable": ([_I], _I),
     "dcrf_profile_reset": ([], _I),
     "dcrf_profile_read": ([_P, _P, _P, _I], _I),
@@ -516,6 +518,32 @@ def dcrf_simplex_project(V: torch.Tensor, stream=None) -> torch.Tensor:
     _check(lib().dcrf_simplex_project(_ptr(V), V.shape[0], V.shape[1], _ptr(Y), _stream(stream)),
            "dcrf_simplex_project")
     return Y
+
+
+def dcrf_check_lattice_tables(point_vertex, point_weight, neighbours, point_offsets, vertex_offsets, stream=None):
+    """Check mode of the lattice tables (device tensors as dcrf_lattice_export
+    returns them, host offsets).  Returns the number of failing entries (0 = valid)."""
+    pv = _dev(point_vertex, torch.int32, "point_vertex", 2)
+    pw = _dev(point_weight, torch.float32, "point_weight", 2)
+    nb = _dev(neighbours, torch.int32, "neighbours", 3)
+    po = np.ascontiguousarray(np.asarray(point_offsets, dtype=np.int64))
+    vo = np.ascontiguousarray(np.asarray(vertex_offsets, dtype=np.int64))
+    bad = np.zeros(1, dtype=np.int64)
+    st = lib().dcrf_check_lattice_tables(_ptr(pv), _ptr(pw), pv.shape[0], pv.shape[1] - 1, _ptr(nb), nb.shape[0],
+                                         po.ctypes.data_as(_P), vo.ctypes.data_as(_P), len(po) - 1,
+                                         bad.ctypes.data_as(_P), _stream(stream))
+    if st not in (0, -1) or (st == -1 and bad[0] == 0):
+        _check(st, "dcrf_check_lattice_tables")
+    return int(bad[0])
+
+
+def dcrf_lattice_validate(lat: Lattice, stream=None) -> int:
+    """Check mode on a lattice's own tables: the number of failing entries (0 = valid)."""
+    bad = np.zeros(1, dtype=np.int64)
+    st = lib().dcrf_lattice_validate(lat.handle, bad.ctypes.data_as(_P), _stream(stream))
+    if st not in (0, -1) or (st == -1 and bad[0] == 0):
+        _check(st, "dcrf_lattice_validate")
+    return int(bad[0])
 
 
 def dcrf_selftest_bounded_wait(lat: Lattice, polls: int, never_complete: bool, stream=None):

@@ -867,6 +867,96 @@ extern "C" dcrf_status dcrf_lattice_status(dcrf_lattice lat, dcrf_stream stream)
     return (dcrf_status)h;
 }
 
+// ---------------------------------------------------------------------------
+// check mode: the tables the kernels index with
+
+__device__ __forceinline__ int image_of(const int64_t *off, int batch, int64_t i) {
+    int lo = 0, hi = batch - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// every corner's vertex is -1 or one of its image's vertices; weights are
+// finite, in [0, 1] and sum to one (1e-5)
+__global__ void k_check_points(const int32_t *__restrict__ pvid, const float *__restrict__ pbary, int64_t n, int d1,
+                               const int64_t *__restrict__ poff, const int64_t *__restrict__ voff, int batch,
+                               unsigned long long *bad) {
+    const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    const int b = image_of(poff, batch, a);
+    float sum = 0.f;
+    int errs = 0;
+    for (int k = 0; k < d1; ++k) {
+        const int v = pvid[a * d1 + k];
+        const float w = pbary[a * d1 + k];
+        if (v != -1 && (v < voff[b] || v >= voff[b + 1])) ++errs;
+        if (!(w >= -1e-6f && w <= 1.f + 1e-6f)) ++errs;
+        sum += w;
+    }
+    if (!(fabsf(sum - 1.f) <= 1e-5f)) ++errs;
+    if (errs) atomicAdd(bad, (unsigned long long)errs);
+}
+
+// every blur neighbour is -1 or a vertex of the same image
+__global__ void k_check_neighbours(const int32_t *__restrict__ nbr, int64_t m, int d1, const int64_t *__restrict__ voff,
+                                   int batch, unsigned long long *bad) {
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= m) return;
+    const int b = image_of(voff, batch, v);
+    int errs = 0;
+    for (int j = 0; j < 2 * d1; ++j) {
+        const int u = nbr[v * 2 * d1 + j];
+        if (u != -1 && (u < voff[b] || u >= voff[b + 1])) ++errs;
+    }
+    if (errs) atomicAdd(bad, (unsigned long long)errs);
+}
+
+extern "C" dcrf_status dcrf_check_lattice_tables(const int32_t *point_vertex, const float *point_weight, int64_t n,
+                                                 int d, const int32_t *neighbours, int64_t m,
+                                                 const int64_t *point_offsets, const int64_t *vertex_offsets,
+                                                 int batch, int64_t *bad_entries, dcrf_stream stream) {
+    if (bad_entries) *bad_entries = 0;
+    if (d < 1 || d > DCRF_MAX_D || n < 0 || m < 0 || batch < 1 || !point_offsets || !vertex_offsets)
+        return DCRF_E_INVAL;
+    if ((n > 0 && (!point_vertex || !point_weight)) || (m > 0 && !neighbours)) return DCRF_E_INVAL;
+    if (point_offsets[0] != 0 || point_offsets[batch] != n || vertex_offsets[0] != 0 || vertex_offsets[batch] != m)
+        return DCRF_E_INVAL;
+    for (int b = 0; b < batch; ++b)
+        if (point_offsets[b + 1] < point_offsets[b] || vertex_offsets[b + 1] < vertex_offsets[b]) return DCRF_E_INVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(s);
+    int64_t *poff, *voff;
+    unsigned long long *bad;
+    DCRF_CHECK_STATUS(sc.get(&poff, (size_t)batch + 1));
+    DCRF_CHECK_STATUS(sc.get(&voff, (size_t)batch + 1));
+    DCRF_CHECK_STATUS(sc.get(&bad, 1));
+    DCRF_TRY(cudaMemcpyAsync(poff, point_offsets, (batch + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    DCRF_TRY(cudaMemcpyAsync(voff, vertex_offsets, (batch + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    DCRF_TRY(cudaMemsetAsync(bad, 0, sizeof(unsigned long long), s));
+    if (n > 0) {
+        k_check_points<<<blocks_for(n, 256), 256, 0, s>>>(point_vertex, point_weight, n, d + 1, poff, voff, batch, bad);
+        DCRF_LAUNCHED();
+    }
+    if (m > 0) {
+        k_check_neighbours<<<blocks_for(m, 256), 256, 0, s>>>(neighbours, m, d + 1, voff, batch, bad);
+        DCRF_LAUNCHED();
+    }
+    unsigned long long h = 0;
+    DCRF_TRY(cudaMemcpyAsync(&h, bad, sizeof(h), cudaMemcpyDeviceToHost, s));
+    DCRF_TRY(cudaStreamSynchronize(s));
+    if (bad_entries) *bad_entries = (int64_t)h;
+    return h ? DCRF_E_INVAL : DCRF_OK;
+}
+
+extern "C" dcrf_status dcrf_lattice_validate(dcrf_lattice lat, int64_t *bad_entries, dcrf_stream stream) {
+    if (!lat) return DCRF_E_INVAL;
+    return dcrf_check_lattice_tables(lat->pvid, lat->pbary, lat->n, lat->d, lat->nbr, lat->m, lat->point_off.data(),
+                                     lat->vert_off.data(), lat->batch, bad_entries, stream);
+}
+
 extern "C" dcrf_status dcrf_lattice_export(dcrf_lattice lat, int32_t *keys, int32_t *point_vertex,
                                            float *point_weight, int32_t *neighbours, dcrf_stream stream) {
     if (!lat) return DCRF_E_INVAL;

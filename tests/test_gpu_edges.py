@@ -157,3 +157,30 @@ def test_bounded_wait_runs_out_and_the_context_survives(dcrf):
     Y = g["y0"].clone()
     rec = dcrf.dcrf_qp_fw(g["phi"], [g["lb"], g["ls"]], p.weights, Y, 5)
     assert np.all(np.isfinite(rec))
+
+
+def test_check_mode_on_lattice_tables(dcrf):
+    # the tables the kernels index with pass the check mode, and host-made
+    # faults in them are counted: a corner pointing into another image, a
+    # vertex id past the end, a negative weight, weights not summing to one,
+    # a blur neighbour past the end
+    probs = [S.make_problem(40, 30, 4, 5, seed=91), S.make_problem(20, 10, 3, 5, seed=92)]
+    g = gpu_setup(dcrf, probs, torch)
+    po = g["off"]
+    for lat in (g["lb"], g["ls"]):
+        assert dcrf.dcrf_lattice_validate(lat) == 0
+        ex = dcrf.dcrf_lattice_export(lat)
+        vo = lat.vertex_offsets
+        pv, pw, nb = ex["point_vertex"], ex["point_weight"], ex["neighbours"]
+        assert dcrf.dcrf_check_lattice_tables(pv, pw, nb, po, vo) == 0
+
+        def bad(pv_=pv, pw_=pw, nb_=nb):
+            return dcrf.dcrf_check_lattice_tables(pv_, pw_, nb_, po, vo)
+
+        x = pv.clone(); x[0, 0] = int(vo[1]); assert bad(pv_=x) == 1           # image 1's vertex for a point of image 0
+        x = pv.clone(); x[-1, 1] = int(lat.m); assert bad(pv_=x) == 1          # past the last vertex
+        w = pw.clone(); w[3, 0] = -0.5; w[3, 1] += 0.5; assert bad(pw_=w) == 1  # negative weight (sum kept)
+        w = pw.clone(); w[5, 0] += 0.25; assert bad(pw_=w) == 1                # weights sum to 1.25
+        n2 = nb.clone(); n2[2, 0, 1] = int(lat.m) + 7; assert bad(nb_=n2) == 1
+        with pytest.raises(ValueError):
+            dcrf.dcrf_check_lattice_tables(pv.float(), pw, nb, po, vo)
