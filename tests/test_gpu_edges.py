@@ -177,10 +177,10 @@ def test_check_mode_on_lattice_tables(dcrf):
         def bad(pv_=pv, pw_=pw, nb_=nb):
             return dcrf.dcrf_check_lattice_tables(pv_, pw_, nb_, po, vo)
 
-        x = pv.clone(); x[0, 0] = int(vo[1]); assert bad(pv_=x) == 1           # image 1's vertex for a point of image 0
-        x = pv.clone(); x[-1, 1] = int(lat.m); assert bad(pv_=x) == 1          # past the last vertex
-        w = pw.clone(); w[3, 0] = -0.5; w[3, 1] += 0.5; assert bad(pw_=w) == 1  # negative weight (sum kept)
-        w = pw.clone(); w[5, 0] += 0.25; assert bad(pw_=w) == 1                # weights sum to 1.25
-        n2 = nb.clone(); n2[2, 0, 1] = int(lat.m) + 7; assert bad(nb_=n2) == 1
+        x = pv.clone(); x[0, 0] = int(vo[1]); assert bad(pv_=x) >= 1           # image 1's vertex for a point of image 0
+        x = pv.clone(); x[-1, 1] = int(lat.m); assert bad(pv_=x) >= 1          # past the last vertex
+        w = pw.clone(); w[3, 0] = -0.5; w[3, 1] += 0.5; assert bad(pw_=w) >= 1  # negative weight (sum kept)
+        w = pw.clone(); w[5, 0] += 0.25; assert bad(pw_=w) >= 1                # weights sum to 1.25
+        n2 = nb.clone(); n2[2, 0, 1] = int(lat.m) + 7; assert bad(nb_=n2) >= 1
         with pytest.raises(ValueError):
             dcrf.dcrf_check_lattice_tables(pv.float(), pw, nb, po, vo)
