@@ -309,6 +309,8 @@ def algorithmic_bytes(kind, n, L, lat_m, lat_d, storage):
     vertex id + weight per simplex corner (8 (d+1) per lattice).  Per lattice
     vertex row of Lp labels: the one-hot splat S s in 32-bit fixed point (4),
     B S s and the sliced B S y in the storage type (esz), Ylat and BY in float32.
+    The line-search kernel also brings Ylat up to date (the previous step's
+    splat folded in); the lattice update then only advances BY.
     """
     Lp = 8 if L <= 8 else (24 if L <= 24 else 64)
     esz = 2 if storage == "f16" else 4
@@ -319,9 +321,12 @@ def algorithmic_bytes(kind, n, L, lat_m, lat_d, storage):
     if kind == "fw_blur":
         return sum(m * Lp * (4 + esz) + d * m * Lp * 2 * esz + (d + 1) * 8 * m for m, d in zip(lat_m, lat_d))
     if kind == "fw_latdot":
-        return sum(m * Lp * (8 + esz) for m in lat_m)
+        # Ylat read and written (the deferred update), S s^{t-1} read and
+        # cleared, S s^t read, B S s^t read, the vertex's image
+        return sum(m * Lp * (20 + esz) + 4 * m for m in lat_m)
     if kind == "fw_latupd":
-        return sum(m * Lp * (24 + esz + half_copy) + 4 * m for m in lat_m)
+        # BY read and written, B S s read, the half copy of BY written
+        return sum(m * Lp * (8 + esz + half_copy) + 4 * m for m in lat_m)
     return 0
 
 
@@ -408,7 +413,7 @@ def main():
 
         # roofline of the dominant kernel (CUDA events on the launching stream)
         lat_m, lat_d = [lb.m, ls.m], [5, 2]
-        per_iter_launch = {"fw_pixel": 1, "fw_blur": max(lat_d) + 1, "fw_latdot": 2, "fw_latupd": 2}
+        per_iter_launch = {"fw_pixel": 1, "fw_blur": max(lat_d) + 1, "fw_latdot": 1, "fw_latupd": 1}
         roof = None
         kinds = {}
         for kind, (cnt, ms) in prof.items():

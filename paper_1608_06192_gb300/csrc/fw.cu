@@ -305,29 +305,50 @@ __global__ void __launch_bounds__(256) k_fw_blur3(BlurSet B, int p) {
 // Lattice dot products for the line search:
 //   0: w s0 sum_v sum_ij mu_ij Ylat[v][i] BS[v][j]   (= <y, K~-part of Psi s>)
 //   1: w s0 sum_v sum_ij mu_ij Slat[v][i] BS[v][j]   (= <s, K~-part of Psi s>)
-// with Slat = Sq 2^-k the value of the fixed-point splat of s;
-// summed per warp in FP32.
+// with Slat = Sq 2^-k the value of the fixed-point splat of s^t, summed per
+// warp in FP32.  Before its dot products the kernel brings Ylat up to date:
+// Ylat = S y^t = Ylat + alpha_{t-1} (S s^{t-1} - Ylat), S s^{t-1} from Sp,
+// which it then clears for the pixel pass's splat of s^{t+1} (alpha_{t-1} = 0
+// at the first iteration).  One launch covers every lattice: block b belongs
+// to lattice m while start[m] <= b < start[m+1].
 struct DotArgs {
-    const Chunk *chunks;    // vertex chunks of lattice `which`
+    const Chunk *chunks[DCRF_MAX_KERNELS];   // vertex chunks of each lattice
+    int start[DCRF_MAX_KERNELS + 1];         // prefix of the chunk counts
+    int64_t voff[DCRF_MAX_KERNELS];          // first per-warp row of each lattice
+    const double *alpha;                     // [batch] alpha_{t-1}
     const float *mu;
     int L;
-    int which;
-    float *vpart;           // [vertex chunks of this lattice][warps][2] per-warp sums
+    float *vpart;                            // [vertex-chunk warps of all lattices][2] per-warp sums
 };
 
 template <int LP, typename T, bool POTTS>
-__global__ void __launch_bounds__(kVertBlock) k_fw_latdot(DotArgs A, FwLat lt) {
-    const Chunk ch = A.chunks[blockIdx.x];
+__global__ void __launch_bounds__(kVertBlock) k_fw_latdot(DotArgs A, FwLats F) {
+    int mm = 0;
+#pragma unroll
+    for (int k = 1; k < DCRF_MAX_KERNELS; ++k)
+        if (k < F.nk && (int)blockIdx.x >= A.start[k]) mm = k;
+    FwLat lt = F.l[0];
+#pragma unroll
+    for (int k = 1; k < DCRF_MAX_KERNELS; ++k)
+        if (k == mm) lt = F.l[k];
+    const int blk = (int)blockIdx.x - A.start[mm];
+    const Chunk ch = A.chunks[mm][blk];
     float part[2] = {0.f, 0.f};
     if ((int)threadIdx.x < ch.count) {
         const int64_t v = ch.begin + threadIdx.x;
         const float inv = __ldg(lt.qs + 1);
+        const float al = (float)A.alpha[lt.vimg[v]];
         float yv[LP], sv[LP], bv[LP];
 #pragma unroll
         for (int g = 0; g < LP / 4; ++g) {
-            float4 a = ld4(lt.Ylat, v * (LP / 4) + g);
-            float4 b = ld4q(lt.Sq, v * (LP / 4) + g, inv);
-            float4 c = ld4((const T *)lt.BS, v * (LP / 4) + g);
+            const int64_t idx = v * (LP / 4) + g;
+            float4 a = ld4(lt.Ylat, idx);
+            const float4 p = ld4q(lt.Sp, idx, inv);
+            const float4 b = ld4q(lt.Sq, idx, inv);
+            const float4 c = ld4((const T *)lt.BS, idx);
+            a.x += al * (p.x - a.x); a.y += al * (p.y - a.y); a.z += al * (p.z - a.z); a.w += al * (p.w - a.w);
+            st4(lt.Ylat, idx, a);
+            reinterpret_cast<uint4 *>(lt.Sp)[idx] = make_uint4(0u, 0u, 0u, 0u);
             yv[4 * g] = a.x; yv[4 * g + 1] = a.y; yv[4 * g + 2] = a.z; yv[4 * g + 3] = a.w;
             sv[4 * g] = b.x; sv[4 * g + 1] = b.y; sv[4 * g + 2] = b.z; sv[4 * g + 3] = b.w;
             bv[4 * g] = c.x; bv[4 * g + 1] = c.y; bv[4 * g + 2] = c.z; bv[4 * g + 3] = c.w;
@@ -355,7 +376,7 @@ __global__ void __launch_bounds__(kVertBlock) k_fw_latdot(DotArgs A, FwLat lt) {
         part[0] = lt.ws0 * py;
         part[1] = lt.ws0 * ps;
     }
-    warp_sums<2>(part, A.vpart + (int64_t)blockIdx.x * (kVertBlock / 32) * 2);
+    warp_sums<2>(part, A.vpart + 2 * (A.voff[mm] + (int64_t)blk * (kVertBlock / 32)));
 }
 
 // Per-image FP64 sums of per-chunk FP32 partials: chunks [range[b], range[b+1])
@@ -477,21 +498,33 @@ __global__ void __launch_bounds__(1024) k_fw_alpha(PartSums P, double *alpha, dc
     }
 }
 
-// Ylat += alpha (Slat - Ylat); BY += alpha (BS - BY) (and its half copy); Sq = 0.
+// BY += alpha (BS - BY) and its half copy, every lattice in one launch
+// (element group idx of lattice m while start[m] <= idx < start[m+1]).
+struct UpdArgs {
+    int64_t start[DCRF_MAX_KERNELS + 1];   // prefix of m * Lp / 4
+    const double *alpha;
+    int G;                                  // Lp / 4
+};
+
 template <typename T>
-__global__ void k_fw_latupd(FwLat lt, int G, const double *alpha) {
-    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= lt.m * G) return;
-    const int64_t v = idx / G;
-    const float al = (float)alpha[lt.vimg[v]];
-    const float inv = __ldg(lt.qs + 1);
-    float4 y = ld4(lt.Ylat, idx), s = ld4q(lt.Sq, idx, inv), by = ld4(lt.BY, idx), bs = ld4((const T *)lt.BS, idx);
-    y.x += al * (s.x - y.x); y.y += al * (s.y - y.y); y.z += al * (s.z - y.z); y.w += al * (s.w - y.w);
+__global__ void k_fw_latupd(FwLats F, UpdArgs U) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= U.start[F.nk]) return;
+    int mm = 0;
+#pragma unroll
+    for (int k = 1; k < DCRF_MAX_KERNELS; ++k)
+        if (k < F.nk && g >= U.start[k]) mm = k;
+    FwLat lt = F.l[0];
+#pragma unroll
+    for (int k = 1; k < DCRF_MAX_KERNELS; ++k)
+        if (k == mm) lt = F.l[k];
+    const int64_t idx = g - U.start[mm];
+    const float al = (float)U.alpha[lt.vimg[idx / U.G]];
+    float4 by = ld4(lt.BY, idx);
+    const float4 bs = ld4((const T *)lt.BS, idx);
     by.x += al * (bs.x - by.x); by.y += al * (bs.y - by.y); by.z += al * (bs.z - by.z); by.w += al * (bs.w - by.w);
-    st4(lt.Ylat, idx, y);
     st4(lt.BY, idx, by);
     if (lt.BYh) st4h(lt.BYh, idx, by);
-    reinterpret_cast<uint4 *>(lt.Sq)[idx] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 // Decision trace: row *counter of trace (when below rows) receives s, the
@@ -618,6 +651,8 @@ struct Solver {
     int *status = nullptr;
     uint8_t *trace = nullptr;                  // [trace_rows][n] decisions s^t, or null
     int trace_rows = 0;
+    uint32_t *sbuf[DCRF_MAX_KERNELS][2] = {};   // the two one-hot splat buffers of each lattice
+    int par = 0;                               // sbuf[m][par] holds S s^t at the start of an iteration
 
     explicit Solver(cudaStream_t st) : s(st), sc(st) {}
 
@@ -674,7 +709,11 @@ struct Solver {
             const size_t cnt = (size_t)(lat->m > 0 ? lat->m : 1) * Lp;
             DCRF_CHECK_STATUS(sc.get(&l.Ylat, cnt));
             DCRF_CHECK_STATUS(sc.get(&l.BY, cnt));
-            DCRF_CHECK_STATUS(sc.get(&l.Sq, cnt));
+            DCRF_CHECK_STATUS(sc.get(&sbuf[m][0], cnt));
+            DCRF_CHECK_STATUS(sc.get(&sbuf[m][1], cnt));
+            DCRF_TRY(cudaMemsetAsync(sbuf[m][1], 0, cnt * sizeof(uint32_t), s));
+            l.Sq = l.St = sbuf[m][0];
+            l.Sp = sbuf[m][1];
             l.BYh = nullptr;
             if (storage == DCRF_STORAGE_F16) DCRF_CHECK_STATUS(sc.get(&l.BYh, cnt));
             char *bs, *tmp;
@@ -724,6 +763,7 @@ struct Solver {
         DCRF_CHECK_STATUS(sc.get(&lin, (size_t)(n > 0 ? n : 1) * L));
         DCRF_CHECK_STATUS(sc.get(&sidx, (size_t)(n > 0 ? n : 1)));
         DCRF_CHECK_STATUS(sc.get(&alpha, (size_t)batch));
+        DCRF_TRY(cudaMemsetAsync(alpha, 0, batch * sizeof(double), s));   // no fold is pending at the start
         DCRF_CHECK_STATUS(sc.get(&counter, 2));
         ticket = counter + 1;
         DCRF_CHECK_STATUS(sc.get(&rec, (size_t)batch * (max_records > 0 ? max_records : 1)));
@@ -928,7 +968,7 @@ struct Solver {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         for (int m = 0; m < nk; ++m)
-            DCRF_TRY(cudaMemsetAsync(F.l[m].Sq, 0, (size_t)(F.l[m].m > 0 ? F.l[m].m : 1) * Lp * sizeof(uint32_t), s));
+            DCRF_TRY(cudaMemsetAsync(F.l[m].St, 0, (size_t)(F.l[m].m > 0 ? F.l[m].m : 1) * Lp * sizeof(uint32_t), s));
         variant = arg;
         std::lock_guard<std::mutex> lk(mu_);
         cache[key] = arg;
@@ -948,7 +988,18 @@ struct Solver {
         return pixel_t<64, T, POT>(Y, phi, start);
     }
 
+    // Splat buffers of this step: Sq = S s^t, Sp = S s^{t-1} (folded and
+    // cleared by the line-search kernel), St = the pixel pass's target.
+    void bind(bool start) {
+        for (int m = 0; m < nk; ++m) {
+            F.l[m].Sq = sbuf[m][par];
+            F.l[m].Sp = sbuf[m][par ^ 1];
+            F.l[m].St = start ? sbuf[m][par] : sbuf[m][par ^ 1];
+        }
+    }
+
     dcrf_status pixel(float *Y, const float *phi, bool start) {
+        bind(start);
         dcrf_status st;
         if (storage == DCRF_STORAGE_F16)
             st = potts ? pixel_lp<__half, true>(Y, phi, start) : pixel_lp<__half, false>(Y, phi, start);
@@ -1091,54 +1142,66 @@ struct Solver {
     }
 
     template <int LPc, typename T, bool POT>
-    dcrf_status latdot_t(int which) {
-        DotArgs A;
-        A.chunks = vchunks[which];
+    dcrf_status latdot_t() {
+        DotArgs A{};
+        A.start[0] = 0;
+        for (int m = 0; m < nk; ++m) {
+            A.chunks[m] = vchunks[m];
+            A.start[m + 1] = A.start[m] + n_vchunks[m];
+            A.voff[m] = voff[m];
+        }
+        A.alpha = alpha;
         A.mu = mu;
         A.L = L;
-        A.which = which;
-        A.vpart = vpart + 2 * voff[which];
-        if (n_vchunks[which] > 0) {
+        A.vpart = vpart;
+        if (A.start[nk] > 0) {
             ProfScope ps(P_FW_LATDOT, s);
-            k_fw_latdot<LPc, T, POT><<<n_vchunks[which], kVertBlock, 0, s>>>(A, F.l[which]);
+            k_fw_latdot<LPc, T, POT><<<A.start[nk], kVertBlock, 0, s>>>(A, F);
             DCRF_LAUNCHED();
         }
         return DCRF_OK;
     }
 
     template <typename T, bool POT>
-    dcrf_status latdot_lp(int which) {
-        if (Lp == 8) return latdot_t<8, T, POT>(which);
-        if (Lp == 24) return latdot_t<24, T, POT>(which);
-        return latdot_t<64, T, POT>(which);
+    dcrf_status latdot_lp() {
+        if (Lp == 8) return latdot_t<8, T, POT>();
+        if (Lp == 24) return latdot_t<24, T, POT>();
+        return latdot_t<64, T, POT>();
     }
 
-    dcrf_status latdot(int which) {
+    dcrf_status latdot() {
         if (storage == DCRF_STORAGE_F16)
-            return potts ? latdot_lp<__half, true>(which) : latdot_lp<__half, false>(which);
-        return potts ? latdot_lp<float, true>(which) : latdot_lp<float, false>(which);
+            return potts ? latdot_lp<__half, true>() : latdot_lp<__half, false>();
+        return potts ? latdot_lp<float, true>() : latdot_lp<float, false>();
     }
 
-    // One Frank-Wolfe iteration, state at (y, s, Sq = S s, BY = B S y).
+    // One Frank-Wolfe iteration, state at (y^t, s^t, Sq = S s^t, BY = B S y^t,
+    // Ylat + alpha_{t-1} (S s^{t-1} - Ylat) = S y^t with S s^{t-1} in Sp).
     dcrf_status iterate(float *Y, const float *phi) {
+        bind(false);
         DCRF_CHECK_STATUS(blur_all());
-        for (int m = 0; m < nk; ++m) DCRF_CHECK_STATUS(latdot(m));
+        DCRF_CHECK_STATUS(latdot());
         {
             ProfScope ps(P_FW_ALPHA, s);
             k_fw_alpha<<<batch, 1024, 0, s>>>(parts(), alpha, rec, counter, ticket, status);
         }
         DCRF_LAUNCHED();
-        const int G = Lp / 4;
-        for (int m = 0; m < nk; ++m) {
-            if (F.l[m].m == 0) continue;
+        UpdArgs U{};
+        U.G = Lp / 4;
+        U.alpha = alpha;
+        U.start[0] = 0;
+        for (int m = 0; m < nk; ++m) U.start[m + 1] = U.start[m] + F.l[m].m * U.G;
+        if (U.start[nk] > 0) {
             ProfScope ps(P_FW_LATUPD, s);
             if (storage == DCRF_STORAGE_F16)
-                k_fw_latupd<__half><<<nblocks(F.l[m].m * G, 256), 256, 0, s>>>(F.l[m], G, alpha);
+                k_fw_latupd<__half><<<nblocks(U.start[nk], 256), 256, 0, s>>>(F, U);
             else
-                k_fw_latupd<float><<<nblocks(F.l[m].m * G, 256), 256, 0, s>>>(F.l[m], G, alpha);
+                k_fw_latupd<float><<<nblocks(U.start[nk], 256), 256, 0, s>>>(F, U);
             DCRF_LAUNCHED();
         }
-        return pixel(Y, phi, false);
+        DCRF_CHECK_STATUS(pixel(Y, phi, false));
+        par ^= 1;   // the splat of s^{t+1} is the next iteration's S s
+        return DCRF_OK;
     }
 
     // Runs `iters` iterations; uses a CUDA graph of two iterations when the
@@ -1260,7 +1323,7 @@ extern "C" dcrf_status dcrf_dc_cccp(const float *unaries, const dcrf_lattice *la
         k_fw_lin<<<nblocks(S.n * L, 256), 256, 0, s>>>(S.n, L, unaries, S.c, S.musum, Y, 2.f, S.lin, S.status);
         DCRF_LAUNCHED();
         for (int m = 0; m < S.nk; ++m)
-            DCRF_TRY(cudaMemsetAsync(S.F.l[m].Sq, 0,
+            DCRF_TRY(cudaMemsetAsync(S.sbuf[m][S.par], 0,
                                      (size_t)(S.F.l[m].m > 0 ? S.F.l[m].m : 1) * S.Lp * sizeof(uint32_t), s));
         DCRF_CHECK_STATUS(S.pixel(Y, inner == 0 ? unaries : nullptr, true));
         DCRF_CHECK_STATUS(S.run(Y, inner, unaries));

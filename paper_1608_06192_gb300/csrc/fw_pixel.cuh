@@ -56,7 +56,14 @@ struct FwLat {
     float *Ylat;     // [m][Lp] S y
     float *BY;       // [m][Lp] B S y (float32 master)
     __half *BYh;     // [m][Lp] half copy of BY sliced by the pixel kernel (half storage only)
-    uint32_t *Sq;    // [m][Lp] S s in fixed point: value = Sq * qs[1] (integer sums: deterministic)
+    // One-hot splats in fixed point (value = entry * qs[1]; integer sums, so
+    // deterministic), two buffers used in turn: at iteration t, Sq holds
+    // S s^t (read by the blur and the line search) and Sp holds S s^{t-1},
+    // which the line-search kernel folds into Ylat and clears; the pixel
+    // pass then splats s^{t+1} into St (= Sp; = Sq in the start pass).
+    uint32_t *Sq;
+    uint32_t *Sp;
+    uint32_t *St;
     const float *qs; // {2^k, 2^-k} of this lattice's fixed point
     void *BS;        // [m][Lp] B S s (float or half)
     void *tmp;       // blur scratch (same type as BS)
@@ -576,7 +583,7 @@ __device__ __forceinline__ bool pixel_chunk(const PixArgs &A, const FwLats &F, c
             const float q = __ldg(lt.qs);
             for (int k = 0; k < lt.d1; ++k) {
                 const int v = __ldg(lt.pvid + a * lt.d1 + k);
-                if (v >= 0) atomicAdd(lt.Sq + (int64_t)v * LP + sb, __float2uint_rn(q * __ldg(lt.pbary + a * lt.d1 + k)));
+                if (v >= 0) atomicAdd(lt.St + (int64_t)v * LP + sb, __float2uint_rn(q * __ldg(lt.pbary + a * lt.d1 + k)));
             }
         }
     }
@@ -741,7 +748,7 @@ __device__ __forceinline__ void pixel3(const PixArgs &A, const FwLats &F, const 
             for (int k = q; k < lt.d1; k += 3) {
                 const int v = __ldg(lt.pvid + a * lt.d1 + k);
                 if (v >= 0)
-                    atomicAdd(lt.Sq + (int64_t)v * LP + sbw, __float2uint_rn(qk * __ldg(lt.pbary + a * lt.d1 + k)));
+                    atomicAdd(lt.St + (int64_t)v * LP + sbw, __float2uint_rn(qk * __ldg(lt.pbary + a * lt.d1 + k)));
             }
         }
     }
