@@ -327,31 +327,58 @@ __global__ void __launch_bounds__(kVertBlock) k_fw_latdot(DotArgs A, FwLats F) {
 #pragma unroll
     for (int k = 1; k < DCRF_MAX_KERNELS; ++k)
         if (k < F.nk && (int)blockIdx.x >= A.start[k]) mm = k;
-    FwLat lt = F.l[0];
+    // the fields of lattice mm (selected one by one: no struct copy in local memory)
+    struct {
+        float *Ylat;
+        uint32_t *Sq, *Sp;
+        const void *BS;
+        const float *qs;
+        const int32_t *vimg;
+        float ws0;
+    } lt = {F.l[0].Ylat, F.l[0].Sq, F.l[0].Sp, F.l[0].BS, F.l[0].qs, F.l[0].vimg, F.l[0].ws0};
 #pragma unroll
     for (int k = 1; k < DCRF_MAX_KERNELS; ++k)
-        if (k == mm) lt = F.l[k];
-    const int blk = (int)blockIdx.x - A.start[mm];
-    const Chunk ch = A.chunks[mm][blk];
+        if (k == mm) {
+            lt.Ylat = F.l[k].Ylat; lt.Sq = F.l[k].Sq; lt.Sp = F.l[k].Sp; lt.BS = F.l[k].BS;
+            lt.qs = F.l[k].qs; lt.vimg = F.l[k].vimg; lt.ws0 = F.l[k].ws0;
+        }
+    int start = A.start[0];
+    const Chunk *chunks = A.chunks[0];
+    int64_t voff = A.voff[0];
+#pragma unroll
+    for (int k = 1; k < DCRF_MAX_KERNELS; ++k)
+        if (k == mm) { start = A.start[k]; chunks = A.chunks[k]; voff = A.voff[k]; }
+    const int blk = (int)blockIdx.x - start;
+    const Chunk ch = chunks[blk];
     float part[2] = {0.f, 0.f};
     if ((int)threadIdx.x < ch.count) {
         const int64_t v = ch.begin + threadIdx.x;
         const float inv = __ldg(lt.qs + 1);
         const float al = (float)A.alpha[lt.vimg[v]];
         float yv[LP], sv[LP], bv[LP];
+        // every load of the row is issued before the first store (the stores
+        // could alias the loads as far as the compiler knows)
+        float4 pv[LP / 4];
 #pragma unroll
         for (int g = 0; g < LP / 4; ++g) {
             const int64_t idx = v * (LP / 4) + g;
-            float4 a = ld4(lt.Ylat, idx);
-            const float4 p = ld4q(lt.Sp, idx, inv);
+            const float4 a = ld4(lt.Ylat, idx);
             const float4 b = ld4q(lt.Sq, idx, inv);
             const float4 c = ld4((const T *)lt.BS, idx);
-            a.x += al * (p.x - a.x); a.y += al * (p.y - a.y); a.z += al * (p.z - a.z); a.w += al * (p.w - a.w);
-            st4(lt.Ylat, idx, a);
-            reinterpret_cast<uint4 *>(lt.Sp)[idx] = make_uint4(0u, 0u, 0u, 0u);
+            pv[g] = ld4q(lt.Sp, idx, inv);
             yv[4 * g] = a.x; yv[4 * g + 1] = a.y; yv[4 * g + 2] = a.z; yv[4 * g + 3] = a.w;
             sv[4 * g] = b.x; sv[4 * g + 1] = b.y; sv[4 * g + 2] = b.z; sv[4 * g + 3] = b.w;
             bv[4 * g] = c.x; bv[4 * g + 1] = c.y; bv[4 * g + 2] = c.z; bv[4 * g + 3] = c.w;
+        }
+#pragma unroll
+        for (int g = 0; g < LP / 4; ++g) {
+            const int64_t idx = v * (LP / 4) + g;
+            float4 a = make_float4(yv[4 * g], yv[4 * g + 1], yv[4 * g + 2], yv[4 * g + 3]);
+            a.x += al * (pv[g].x - a.x); a.y += al * (pv[g].y - a.y);
+            a.z += al * (pv[g].z - a.z); a.w += al * (pv[g].w - a.w);
+            yv[4 * g] = a.x; yv[4 * g + 1] = a.y; yv[4 * g + 2] = a.z; yv[4 * g + 3] = a.w;
+            st4(lt.Ylat, idx, a);
+            reinterpret_cast<uint4 *>(lt.Sp)[idx] = make_uint4(0u, 0u, 0u, 0u);
         }
         float py = 0.f, ps = 0.f;
         if (POTTS) {
@@ -376,7 +403,7 @@ __global__ void __launch_bounds__(kVertBlock) k_fw_latdot(DotArgs A, FwLats F) {
         part[0] = lt.ws0 * py;
         part[1] = lt.ws0 * ps;
     }
-    warp_sums<2>(part, A.vpart + 2 * (A.voff[mm] + (int64_t)blk * (kVertBlock / 32)));
+    warp_sums<2>(part, A.vpart + 2 * (voff + (int64_t)blk * (kVertBlock / 32)));
 }
 
 // Per-image FP64 sums of per-chunk FP32 partials: chunks [range[b], range[b+1])
@@ -502,6 +529,7 @@ __global__ void __launch_bounds__(1024) k_fw_alpha(PartSums P, double *alpha, dc
 // (element group idx of lattice m while start[m] <= idx < start[m+1]).
 struct UpdArgs {
     int64_t start[DCRF_MAX_KERNELS + 1];   // prefix of m * Lp / 4
+    int64_t total;                          // start[nk]
     const double *alpha;
     int G;                                  // Lp / 4
 };
@@ -509,22 +537,29 @@ struct UpdArgs {
 template <typename T>
 __global__ void k_fw_latupd(FwLats F, UpdArgs U) {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g >= U.start[F.nk]) return;
+    if (g >= U.total) return;
     int mm = 0;
 #pragma unroll
     for (int k = 1; k < DCRF_MAX_KERNELS; ++k)
         if (k < F.nk && g >= U.start[k]) mm = k;
-    FwLat lt = F.l[0];
+    float *BY = F.l[0].BY;
+    const void *BS = F.l[0].BS;
+    __half *BYh = F.l[0].BYh;
+    const int32_t *vimg = F.l[0].vimg;
 #pragma unroll
     for (int k = 1; k < DCRF_MAX_KERNELS; ++k)
-        if (k == mm) lt = F.l[k];
-    const int64_t idx = g - U.start[mm];
-    const float al = (float)U.alpha[lt.vimg[idx / U.G]];
-    float4 by = ld4(lt.BY, idx);
-    const float4 bs = ld4((const T *)lt.BS, idx);
+        if (k == mm) { BY = F.l[k].BY; BS = F.l[k].BS; BYh = F.l[k].BYh; vimg = F.l[k].vimg; }
+    int64_t start = U.start[0];
+#pragma unroll
+    for (int k = 1; k < DCRF_MAX_KERNELS; ++k)
+        if (k == mm) start = U.start[k];
+    const int64_t idx = g - start;
+    const float al = (float)U.alpha[vimg[idx / U.G]];
+    float4 by = ld4(BY, idx);
+    const float4 bs = ld4((const T *)BS, idx);
     by.x += al * (bs.x - by.x); by.y += al * (bs.y - by.y); by.z += al * (bs.z - by.z); by.w += al * (bs.w - by.w);
-    st4(lt.BY, idx, by);
-    if (lt.BYh) st4h(lt.BYh, idx, by);
+    st4(BY, idx, by);
+    if (BYh) st4h(BYh, idx, by);
 }
 
 // Decision trace: row *counter of trace (when below rows) receives s, the
@@ -1191,6 +1226,7 @@ struct Solver {
         U.alpha = alpha;
         U.start[0] = 0;
         for (int m = 0; m < nk; ++m) U.start[m + 1] = U.start[m] + F.l[m].m * U.G;
+        U.total = U.start[nk];
         if (U.start[nk] > 0) {
             ProfScope ps(P_FW_LATUPD, s);
             if (storage == DCRF_STORAGE_F16)
