@@ -272,8 +272,10 @@ class ClockSampler:
 
 def measured_traffic(kind, n):
     """DRAM bytes per launch of the pixel kernel from the committed ncu capture
-    (profiles/fw_pixel_traffic.json), scaled by pixels; None when the kernel's
-    source (csrc/fw_pixel.cuh) changed since the capture, or for other kernels."""
+    (profiles/fw_pixel_traffic.json: a 1-pass capture of dram__bytes_read.sum +
+    dram__bytes_write.sum on the benchmark's own batch), scaled by pixels when
+    the batch differs; None when the kernel's source (csrc/fw_pixel.cuh)
+    changed since the capture, or for other kernels."""
     if kind != "fw_pixel":
         return None
     try:
@@ -282,7 +284,7 @@ def measured_traffic(kind, n):
         src = open(os.path.join(ROOT, "paper_1608_06192_gb300", "csrc", "fw_pixel.cuh"), "rb").read()
         if hashlib.sha1(src).hexdigest() != rec["source_sha1"]:
             return None
-        return int(rec["dram_bytes_per_pixel"] * n)
+        return int(rec["dram_bytes_per_launch"] * n / rec["pixels"])
     except (OSError, KeyError, ValueError):
         return None
 
