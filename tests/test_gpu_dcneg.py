@@ -97,3 +97,23 @@ def test_dcneg_headline_size(dcrf):
     assert np.all(np.diff(e[:, 0]) <= 1e-5 * np.abs(e).max())
     np.testing.assert_allclose(Y.sum(1), 1.0, atol=1e-5)
     assert Y.min() >= -1e-6
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-4), ("f16", 2e-3)])
+def test_dcneg_first_step_elementwise(dcrf, storage, tol):
+    # One outer step from y0 is y1 = Proj(v), v = -(phi + mu F)/(2 sum_w),
+    # F = K~y0 + K~^T y0 (Appendix C, Potts).  The projection onto the simplex
+    # is 1-Lipschitz in the 2-norm, so |y1 - y1_oracle| <= sqrt(L) |dv|_inf
+    # with |dv| <= (L - 1) |dF|_inf / (2 sum_w) and |dF| <= 2 tol max(K~1) by
+    # the filter tolerance (K~ >= 0, 0 <= y0 <= 1): y1 is compared per
+    # element against that bound.
+    probs = [S.qp_small(), S.make_problem(80, 60, 8, 21, seed=22)]
+    for p in probs:
+        g, Y, e = _run(dcrf, [p], 1, storage=storage)
+        c = oracle_crf(p)
+        y_o, _ = qp.cccp_dc_neg(c, p.y0, 1, 0)
+        L, sw = p.n_labels, c.kernel.sum_w
+        bound = np.sqrt(L) * (L - 1) * 2 * tol * float((c.c_raw + sw).max()) / (2 * sw)
+        err = float(np.abs(Y.astype(np.float64) - y_o).max())
+        print(f"\n{storage} {p.width}x{p.height} L={L}: max |dy| {err:.3g} (bound {bound:.3g})")
+        assert err <= bound
