@@ -671,7 +671,8 @@ struct Solver {
     Chunk *chunks_pb[3] = {nullptr, nullptr, nullptr};   // 256-, 128- and 80-pixel chunk lists
     int n_chunks_pb[3] = {0, 0, 0};
     int variant = -1;                          // chosen pixel-kernel variant
-    int blur_variant = -1;                     // chosen blur kernel (0: row per thread, 1: label-split)
+    int blur_variant = -1;                     // chosen blur kernel of every pass, 2 bits per pass
+                                               // (0: row per thread, 1: label-split, 2: persistent)
     std::vector<Chunk *> vchunks;
     std::vector<int> n_vchunks;
     float *mu = nullptr, *musum = nullptr, *c = nullptr, *lin = nullptr;
@@ -1077,12 +1078,19 @@ struct Solver {
     }
 
     template <int LPc, typename T>
-    dcrf_status blur_passes(const BlurSet &B, int dmax, int variant_) {
-        for (int p = 0; p < dmax; ++p) {
+    dcrf_status blur_passes(const BlurSet &B, int dmax, int code) {
+        for (int p = 0; p < dmax; ++p) DCRF_CHECK_STATUS((blur_pass<LPc, T>(B, p, (code >> (2 * p)) & 3)));
+        return DCRF_OK;
+    }
+
+    // Jacobi pass p of every lattice that has it, with blur kernel variant_.
+    template <int LPc, typename T>
+    dcrf_status blur_pass(const BlurSet &B, int p, int variant_) {
+        {
             int active = 0;
             while (active < nk && B.l[active].d1 > p) ++active;
             const int64_t work = B.start[active];
-            if (work == 0) continue;
+            if (work == 0) return DCRF_OK;
             ProfScope ps(P_FW_BLUR, s);
             if (variant_ == 1) {
                 constexpr int RW = 32 / (LPc / 8);
@@ -1115,14 +1123,22 @@ struct Solver {
     }
 
     // Blur tuner: a vertex row per thread (0), label-split rows (1) or the
-    // persistent form with the neighbour pair loaded a row ahead (2), timed on
-    // this problem's lattices (the blur only reads Sq and writes BS and tmp,
-    // which every iteration overwrites) and cached per (Lp, storage, size bucket).
+    // persistent form with the neighbour pair loaded a row ahead (2), timed
+    // pass by pass on this problem's lattices (the blur only reads Sq and
+    // writes BS and tmp, which every iteration overwrites; the passes that
+    // only the higher-dimensional lattice has are smaller and can favour
+    // another kernel) and cached per (Lp, storage, size bucket).
+    static int blur_code_all(int v) {
+        int code = 0;
+        for (int p = 0; p < DCRF_MAX_D + 1; ++p) code |= v << (2 * p);
+        return code;
+    }
+
     template <int LPc, typename T>
     dcrf_status tune_blur(const BlurSet &B, int dmax) {
         if (const char *force = std::getenv("DCRF_BLUR_VARIANT")) {   // testing hook
             const int f = std::atoi(force);
-            blur_variant = (f == 1 || f == 2) ? f : 0;
+            blur_variant = blur_code_all((f == 1 || f == 2) ? f : 0);
             return DCRF_OK;
         }
         static std::mutex mu_;
@@ -1142,20 +1158,24 @@ struct Solver {
         cudaEvent_t e0, e1;
         DCRF_TRY(cudaEventCreate(&e0));
         DCRF_TRY(cudaEventCreate(&e1));
-        float best = 1e30f;
         int arg = 0;
-        for (int v = 0; v < 3; ++v) {
-            DCRF_CHECK_STATUS((blur_passes<LPc, T>(B, dmax, v)));   // warm-up
-            DCRF_TRY(cudaEventRecord(e0, s));
-            for (int r = 0; r < 3; ++r) DCRF_CHECK_STATUS((blur_passes<LPc, T>(B, dmax, v)));
-            DCRF_TRY(cudaEventRecord(e1, s));
-            DCRF_TRY(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            DCRF_TRY(cudaEventElapsedTime(&ms, e0, e1));
-            if (std::getenv("DCRF_TUNE_LOG"))
-                std::fprintf(stderr, "dcrf tune: blur Lp=%d storage=%d rows=%lld variant %d: %.1f us\n", LPc, storage,
-                             (long long)work, v, 1000.f * ms / 3.f);
-            if (ms < best) { best = ms; arg = v; }
+        for (int p = 0; p < dmax; ++p) {
+            float best = 1e30f;
+            int bv = 0;
+            for (int v = 0; v < 3; ++v) {
+                DCRF_CHECK_STATUS((blur_pass<LPc, T>(B, p, v)));   // warm-up
+                DCRF_TRY(cudaEventRecord(e0, s));
+                for (int r = 0; r < 3; ++r) DCRF_CHECK_STATUS((blur_pass<LPc, T>(B, p, v)));
+                DCRF_TRY(cudaEventRecord(e1, s));
+                DCRF_TRY(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                DCRF_TRY(cudaEventElapsedTime(&ms, e0, e1));
+                if (std::getenv("DCRF_TUNE_LOG"))
+                    std::fprintf(stderr, "dcrf tune: blur Lp=%d storage=%d rows=%lld pass %d variant %d: %.1f us\n",
+                                 LPc, storage, (long long)work, p, v, 1000.f * ms / 3.f);
+                if (ms < best) { best = ms; bv = v; }
+            }
+            arg |= bv << (2 * p);
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
