@@ -95,6 +95,9 @@ dcrf_status dcrf_features(const float *rgb, const int32_t *widths, const int32_t
  * stream once (to read the vertex count) and returns DCRF_E_TABLE_FULL or
  * DCRF_E_KEY_RANGE when the device reported it; *out is then NULL.
  * A lattice is immutable after the build and may be read from any stream.
+ * Its arrays come from the library's device pool (see dcrf_pool_trim) of the
+ * stream's device; dcrf_lattice_destroy synchronises the device and returns
+ * them to that pool.
  */
 dcrf_status dcrf_lattice_build(const float *features, int64_t n, int d, dcrf_stream stream,
                                dcrf_lattice *out);

@@ -54,6 +54,7 @@ struct dcrf_lattice_s {
     int32_t *vimg = nullptr;         // [m] image of each vertex
     float *ones = nullptr;           // [n] (K~_lattice 1)_a, s0 included
     int *status = nullptr;           // device status word (first error wins)
+    int device = -1;                 // the device whose memory pool holds the arrays
 };
 
 // Records the first device-side error.

@@ -12,6 +12,7 @@
 //      once both uploads have landed;
 //   5. download y and synchronise.
 // With pageable host memory the uploads still work but no longer overlap.
+#include <chrono>
 #include <cstdio>
 #include <cstdlib>
 
@@ -37,29 +38,38 @@ struct EventGuard {
 };
 
 // DCRF_HOST_LOG=1: CUDA events at the phase boundaries, printed to stderr
-// as milliseconds after the call's start once the call has synchronised.
+// as milliseconds after the call's start once the call has synchronised,
+// beside the host clock when each mark was issued.
 struct PhaseLog {
     static constexpr int kMax = 8;
     bool on = false;
     int n = 0;
     cudaEvent_t ev[kMax] = {};
     const char *name[kMax] = {};
+    double host_ms[kMax] = {};
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
     PhaseLog() {
         const char *e = std::getenv("DCRF_HOST_LOG");
         on = e && e[0] == '1';
+    }
+    double host_now() const {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
     void mark(const char *what, cudaStream_t st) {
         if (!on || n >= kMax) return;
         if (cudaEventCreate(&ev[n]) != cudaSuccess) return;
         cudaEventRecord(ev[n], st);
+        host_ms[n] = host_now();
         name[n++] = what;
     }
     void print() {
         for (int i = 1; i < n; ++i) {
             float ms = 0.f;
             cudaEventElapsedTime(&ms, ev[0], ev[i]);
-            std::fprintf(stderr, "dcrf host: %-22s %8.3f ms\n", name[i], ms);
+            std::fprintf(stderr, "dcrf host: %-22s %8.3f ms (issued at host %8.3f ms)\n", name[i], ms, host_ms[i]);
         }
+        if (on) std::fprintf(stderr, "dcrf host: %-22s host %8.3f ms (first mark at %.3f)\n", "synchronised", host_now(),
+                             host_ms[0]);
     }
     ~PhaseLog() {
         for (int i = 0; i < n; ++i) cudaEventDestroy(ev[i]);

@@ -580,17 +580,25 @@ extern "C" dcrf_status dcrf_filter_adjoint(dcrf_lattice lat, const float *U, int
 // ---------------------------------------------------------------------------
 // build driver
 
+// The lattice's arrays come from the library's stream-ordered pool of its
+// device (a build maps no new memory once the pool holds enough, and a destroy
+// unmaps none).  They are freed on that device's legacy default stream once
+// no work that may read them is left (callers synchronise first).
+template <typename T>
+static dcrf_status lattice_alloc(T **p, size_t count, cudaStream_t s) {
+    return dcrf_alloc(p, count > 0 ? count : 1, s);
+}
+
 static void lattice_free(dcrf_lattice lat) {
     if (!lat) return;
-    cudaFree(lat->point_off_d);
-    cudaFree(lat->vert_off_d);
-    cudaFree(lat->pvid);
-    cudaFree(lat->pbary);
-    cudaFree(lat->keys);
-    cudaFree(lat->nbr);
-    cudaFree(lat->vimg);
-    cudaFree(lat->ones);
-    cudaFree(lat->status);
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (lat->device >= 0 && lat->device != cur) cudaSetDevice(lat->device);
+    void *arrays[] = {lat->point_off_d, lat->vert_off_d, lat->pvid, lat->pbary, lat->keys,
+                      lat->nbr,         lat->vimg,       lat->ones, lat->status};
+    for (void *p : arrays)
+        if (p) cudaFreeAsync(p, 0);
+    if (lat->device >= 0 && lat->device != cur) cudaSetDevice(cur);
     delete lat;
 }
 
@@ -728,9 +736,9 @@ static dcrf_status build_typed(dcrf_lattice lat, const float *feat, cudaStream_t
         DCRF_LAUNCHED();
     }
 
-    DCRF_TRY(cudaMalloc(&lat->keys, (m > 0 ? m : 1) * D * sizeof(int32_t)));
-    DCRF_TRY(cudaMalloc(&lat->vimg, (m > 0 ? m : 1) * sizeof(int32_t)));
-    DCRF_TRY(cudaMalloc(&lat->nbr, (m > 0 ? m : 1) * D1 * 2 * sizeof(int32_t)));
+    DCRF_CHECK_STATUS(lattice_alloc(&lat->keys, (size_t)m * D, s));
+    DCRF_CHECK_STATUS(lattice_alloc(&lat->vimg, (size_t)m, s));
+    DCRF_CHECK_STATUS(lattice_alloc(&lat->nbr, (size_t)m * D1 * 2, s));
     k_finalize_slots<D><<<blocks_for(slots, 256), 256, 0, s>>>(table, slots, ids, base_d, batch, lat->keys,
                                                                lat->vimg);
     DCRF_LAUNCHED();
@@ -793,17 +801,18 @@ extern "C" dcrf_status dcrf_lattice_build_batch(const float *features, const int
     lat->batch = batch;
     lat->point_off.assign(offsets, offsets + batch + 1);
     const int D1 = d + 1;
-    cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMalloc(&lat->point_off_d, (batch + 1) * sizeof(int64_t));
-    if (e == cudaSuccess) e = cudaMalloc(&lat->vert_off_d, (batch + 1) * sizeof(int64_t));
-    if (e == cudaSuccess) e = cudaMalloc(&lat->pvid, (n > 0 ? n : 1) * D1 * sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&lat->pbary, (n > 0 ? n : 1) * D1 * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&lat->ones, (n > 0 ? n : 1) * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&lat->status, sizeof(int));
-    if (e != cudaSuccess) { lattice_free(lat); return DCRF_E_NOMEM; }
-    e = cudaMemcpyAsync(lat->point_off_d, offsets, (batch + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    if (cudaStreamGetDevice(s, &lat->device) != cudaSuccess) { delete lat; return DCRF_E_CUDA; }
+    dcrf_status ast = DCRF_OK;
+    if (ast == DCRF_OK) ast = lattice_alloc(&lat->point_off_d, (size_t)batch + 1, s);
+    if (ast == DCRF_OK) ast = lattice_alloc(&lat->vert_off_d, (size_t)batch + 1, s);
+    if (ast == DCRF_OK) ast = lattice_alloc(&lat->pvid, (size_t)n * D1, s);
+    if (ast == DCRF_OK) ast = lattice_alloc(&lat->pbary, (size_t)n * D1, s);
+    if (ast == DCRF_OK) ast = lattice_alloc(&lat->ones, (size_t)n, s);
+    if (ast == DCRF_OK) ast = lattice_alloc(&lat->status, 1, s);
+    if (ast != DCRF_OK) { cudaStreamSynchronize(s); lattice_free(lat); return ast; }
+    cudaError_t e = cudaMemcpyAsync(lat->point_off_d, offsets, (batch + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(lat->status, 0, sizeof(int), s);
-    if (e != cudaSuccess) { lattice_free(lat); return DCRF_E_CUDA; }
+    if (e != cudaSuccess) { cudaStreamSynchronize(s); lattice_free(lat); return DCRF_E_CUDA; }
     dcrf_status st;
     switch (d) {
     case 1: st = build_typed<1>(lat, features, s); break;
