@@ -559,13 +559,7 @@ __global__ void k_fw_latupd(FwLats F, UpdArgs U) {
     const float4 bs = ld4((const T *)BS, idx);
     by.x += al * (bs.x - by.x); by.y += al * (bs.y - by.y); by.z += al * (bs.z - by.z); by.w += al * (bs.w - by.w);
     st4(BY, idx, by);
-    if (BYh) {
-        // the half copy is what the pixel pass gathers next: kept in L2
-        __half2 lo = __floats2half2_rn(by.x, by.y), hi = __floats2half2_rn(by.z, by.w);
-        const uint32_t u0 = *reinterpret_cast<uint32_t *>(&lo), u1 = *reinterpret_cast<uint32_t *>(&hi);
-        asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;\n" ::"l"(BYh + 4 * idx), "r"(u0), "r"(u1),
-                     "l"(l2_policy_last()) : "memory");
-    }
+    if (BYh) st4h(BYh, idx, by);
 }
 
 // Decision trace: row *counter of trace (when below rows) receives s, the
@@ -951,8 +945,6 @@ struct Solver {
                 DCRF_PIX_CASE(16);
                 DCRF_PIX_CASE(17);
                 DCRF_PIX_CASE(18);
-                DCRF_PIX_CASE(19);
-                DCRF_PIX_CASE(20);
             default: return pixel_v<LPc, T, POT, kPixPB[0], kPixMB[0], kPixMode[0]>(Y, phi, start, al);
             }
 #undef DCRF_PIX_CASE

@@ -24,14 +24,11 @@ namespace {
 // kL21 fixes L = 21 at compile time (the label count of the segmentation
 // workloads): the loops over the padded 24 labels lose their runtime bounds
 // and the padding labels' accumulators and FMAs go away.
-// kHint gives the L2 eviction-priority hints of the access pattern: the
-// corner rows of B S y (read nine times per pixel, 70 MB at 32 x 500x375)
-// are kept (evict_last), the streamed y and lin tiles go first (evict_first).
-constexpr int kFix = 1, kF2 = 2, kL3 = 4, kEarly = 8, kBulk = 16, kLean = 32, kL21 = 64, kHint = 128;
-constexpr int kPixVariants = 21;
+constexpr int kFix = 1, kF2 = 2, kL3 = 4, kEarly = 8, kBulk = 16, kLean = 32, kL21 = 64;
+constexpr int kPixVariants = 19;
 constexpr int kPixPB[kPixVariants] = {256, 128, 256, 128, 256, 80, 128, 256, 128, 128,
-                                      128, 128, 128, 128, 128, 128, 128, 128, 128, 128, 128};
-constexpr int kPixMB[kPixVariants] = {4, 8, 3, 6, 3, 0, 6, 3, 6, 8, 7, 8, 7, 6, 7, 8, 7, 8, 6, 7, 8};
+                                      128, 128, 128, 128, 128, 128, 128, 128, 128};
+constexpr int kPixMB[kPixVariants] = {4, 8, 3, 6, 3, 0, 6, 3, 6, 8, 7, 8, 7, 6, 7, 8, 7, 8, 6};
 constexpr int kPixMode[kPixVariants] = {0,           0,           kFix,         kFix,
                                         kFix | kF2,  kL3,         kFix | kEarly, kFix | kEarly,
                                         kFix | kF2 | kEarly, kFix | kEarly, kFix | kF2 | kEarly,
@@ -40,9 +37,7 @@ constexpr int kPixMode[kPixVariants] = {0,           0,           kFix,         
                                         kFix | kF2 | kEarly | kBulk | kLean,
                                         kFix | kF2 | kEarly | kBulk | kLean | kL21,
                                         kFix | kF2 | kEarly | kBulk | kLean | kL21,
-                                        kFix | kF2 | kEarly | kBulk | kLean | kL21,
-                                        kFix | kF2 | kEarly | kBulk | kLean | kL21 | kHint,
-                                        kFix | kF2 | kEarly | kBulk | kLean | kL21 | kHint};
+                                        kFix | kF2 | kEarly | kBulk | kLean | kL21};
 // whether variant v can run a problem with L labels
 constexpr bool pixel_variant_fits(int v, int L) { return (kPixMode[v] & kL21) == 0 || L == 21; }
 // chunk list of a pixel-block size (256, 128 or 80 pixels)
@@ -177,33 +172,6 @@ __device__ __forceinline__ void ld8(const __half *p, int64_t row, int LP, int h,
     o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y; o[4] = c.x; o[5] = c.y; o[6] = d.x; o[7] = d.y;
 }
 
-// L2 cache policies: keep (evict_last) or let go first (evict_first).
-__device__ __forceinline__ uint64_t l2_policy_last() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
-    return p;
-}
-__device__ __forceinline__ uint64_t l2_policy_first() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
-    return p;
-}
-// ld8 of a half row with an L2 cache policy
-__device__ __forceinline__ void ld8_hint(const __half *p, int64_t row, int LP, int h, uint64_t pol, float (&o)[8]) {
-    uint4 raw;
-    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;\n"
-                 : "=r"(raw.x), "=r"(raw.y), "=r"(raw.z), "=r"(raw.w)
-                 : "l"(p + row * LP + 8 * h), "l"(pol));
-    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&raw.x));
-    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&raw.y));
-    const float2 c = __half22float2(*reinterpret_cast<const __half2 *>(&raw.z));
-    const float2 d = __half22float2(*reinterpret_cast<const __half2 *>(&raw.w));
-    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y; o[4] = c.x; o[5] = c.y; o[6] = d.x; o[7] = d.y;
-}
-__device__ __forceinline__ void ld8_hint(const float *p, int64_t row, int LP, int h, uint64_t, float (&o)[8]) {
-    ld8(p, row, LP, h, o);
-}
-
 // s + e = a + b exactly (Knuth's two-sum; no FMA contraction applies).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     s = a + b;
@@ -278,19 +246,6 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, long long pol
         if (done) return true;
     }
     return false;
-}
-// the same with an L2 cache policy
-__device__ __forceinline__ void bulk_g2s_hint(void *dst, const void *src, unsigned bytes, unsigned long long *bar,
-                                              uint64_t pol) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;\n"
-        ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol) : "memory");
-}
-__device__ __forceinline__ void bulk_s2g_hint(void *dst, const void *src, unsigned bytes, uint64_t pol) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;\n" ::"l"(dst),
-                 "r"(smem_addr(src)), "r"(bytes), "l"(pol) : "memory");
-    asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
-    asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
 }
 // shared -> global bulk store of this thread; returns after the shared source was read
 __device__ __forceinline__ void bulk_s2g(void *dst, const void *src, unsigned bytes) {
@@ -384,9 +339,8 @@ __device__ __forceinline__ void acc8(float (&acc)[LP], int h, float w, const flo
 // K~ y' for the two-kernel case with d+1 = DA and DB corners: every vertex id
 // and weight is loaded first, then every corner row, so that the dependent
 // loads of one pixel overlap (an absent corner reads row 0 with weight 0).
-template <int LP, typename TB, int DA, int DB, bool F2, bool HINT>
+template <int LP, typename TB, int DA, int DB, bool F2>
 __device__ __forceinline__ void gather_pair(const FwLat &la, const FwLat &lb, int64_t a, float (&ky)[LP]) {
-    const uint64_t pol = HINT ? l2_policy_last() : 0ull;
     int v[DA + DB];
     float w[DA + DB];
 #pragma unroll
@@ -407,8 +361,7 @@ __device__ __forceinline__ void gather_pair(const FwLat &la, const FwLat &lb, in
 #pragma unroll
         for (int h = 0; h < LP / 8; ++h) {
             float o[8];
-            if (HINT) ld8_hint(k < DA ? sa : sb, vk, LP, h, pol, o);
-            else ld8(k < DA ? sa : sb, vk, LP, h, o);
+            ld8(k < DA ? sa : sb, vk, LP, h, o);
             acc8<LP, F2>(ky, h, wk, o);
         }
     }
@@ -442,7 +395,7 @@ __device__ __forceinline__ bool pixel_chunk(const PixArgs &A, const FwLats &F, c
         // K~ y' gathered from the lattice, eight labels at a time
         constexpr bool F2 = (MODE & kF2) != 0;
         const bool fixed = (MODE & kFix) && F.nk == 2 && F.l[0].d1 == 6 && F.l[1].d1 == 3;
-        if (fixed) gather_pair<LP, TB, 6, 3, F2, (MODE & kHint) != 0>(F.l[0], F.l[1], a, ky);
+        if (fixed) gather_pair<LP, TB, 6, 3, F2>(F.l[0], F.l[1], a, ky);
 #pragma unroll
         for (int mm = 0; mm < DCRF_MAX_KERNELS; ++mm) {
             if (fixed || mm >= F.nk) break;
@@ -839,14 +792,8 @@ __global__ void __launch_bounds__(PB, MB) k_fw_pixel(PixArgs A, FwLats F) {
             const int64_t base = ch.begin * (int64_t)A.L;
             const unsigned bytes = (unsigned)(ch.count * A.L) * 4u;
             mbar_expect_tx(tbar, 2u * bytes);
-            if constexpr ((MODE & kHint) != 0) {
-                const uint64_t pol = l2_policy_first();
-                bulk_g2s_hint(sy, A.Y + base, bytes, tbar, pol);
-                bulk_g2s_hint(sl, A.lin + base, bytes, tbar, pol);
-            } else {
-                bulk_g2s(sy, A.Y + base, bytes, tbar);
-                bulk_g2s(sl, A.lin + base, bytes, tbar);
-            }
+            bulk_g2s(sy, A.Y + base, bytes, tbar);
+            bulk_g2s(sl, A.lin + base, bytes, tbar);
         }
     } else {
         tile_load_async(A, ch, sy, sl);
@@ -862,13 +809,8 @@ __global__ void __launch_bounds__(PB, MB) k_fw_pixel(PixArgs A, FwLats F) {
     __syncthreads();
     if (A.alpha != nullptr && tile_ok) {
         if (tbar) {
-            if (threadIdx.x == 0) {
-                const unsigned bytes = (unsigned)(ch.count * A.L) * 4u;
-                if constexpr ((MODE & kHint) != 0)
-                    bulk_s2g_hint(A.Y + ch.begin * (int64_t)A.L, sy, bytes, l2_policy_first());
-                else
-                    bulk_s2g(A.Y + ch.begin * (int64_t)A.L, sy, bytes);
-            }
+            if (threadIdx.x == 0)
+                bulk_s2g(A.Y + ch.begin * (int64_t)A.L, sy, (unsigned)(ch.count * A.L) * 4u);
         } else {
             tile_store(A, ch, sy);
         }
