@@ -259,6 +259,12 @@ dcrf_status dcrf_qp_fw_backward(const float *unaries, const dcrf_lattice *lattic
 dcrf_status dcrf_dc_cccp(const float *unaries, const dcrf_lattice *lattices, const float *weights,
                          int n_kernels, const float *compat, int L, int outer, int inner, float *Y,
                          double *qp_energy, int storage, dcrf_stream stream);
+/* dcrf_dc_cccp that also returns the decisions: s_trace, device uint8
+ * [outer * inner][N], row o * inner + i = the conditional gradient of inner
+ * Frank-Wolfe iteration i of outer step o (as dcrf_qp_fw_trace); may be NULL. */
+dcrf_status dcrf_dc_cccp_trace(const float *unaries, const dcrf_lattice *lattices, const float *weights,
+                               int n_kernels, const float *compat, int L, int outer, int inner, float *Y,
+                               double *qp_energy, uint8_t *s_trace, int storage, dcrf_stream stream);
 
 /*
  * CCCP on the DC relaxation for negative semi-definite compatibilities

@@ -70,8 +70,13 @@ def frank_wolfe(crf, y0, iters: int, lin=None, P_y=None, decisions=None, on_step
     return y, P_y, np.array(recs).reshape(-1, 5)
 
 
-def cccp_dc_gen(crf, y0, outer: int, inner: int):
-    """Returns (y, qp_energies[outer+1]) with S_QP after every outer step."""
+def cccp_dc_gen(crf, y0, outer: int, inner: int, decisions=None, on_step=None):
+    """Returns (y, qp_energies[outer+1]) with S_QP after every outer step.
+
+    decisions: optional [outer * inner][n] vertices replayed by the inner
+    Frank-Wolfe runs (row o * inner + i for inner iteration i of outer step o);
+    on_step(o * inner + t, g, s_idx) as in frank_wolfe.
+    """
     y = np.array(y0, dtype=np.float64)
     P_y = crf.psi_plus_D(y)
 
@@ -79,9 +84,11 @@ def cccp_dc_gen(crf, y0, outer: int, inner: int):
         return float(np.sum(crf.phi * y) + np.sum(y * P_y) - np.sum(crf.d * y * y))
 
     energies = [s_qp(y, P_y)]
-    for _ in range(outer):
+    for o in range(outer):
         lin = crf.phi - 2.0 * crf.d * y
-        y, P_y, _ = frank_wolfe(crf, y, inner, lin=lin, P_y=P_y)
+        dec = None if decisions is None else decisions[o * inner:(o + 1) * inner]
+        step = None if on_step is None else (lambda t, g, s, o=o: on_step(o * inner + t, g, s))
+        y, P_y, _ = frank_wolfe(crf, y, inner, lin=lin, P_y=P_y, decisions=dec, on_step=step)
         energies.append(s_qp(y, P_y))
     return y, np.array(energies)
 

@@ -56,6 +56,7 @@ _SIGS = {
     "dcrf_filter_static_capacity": ([], ctypes.c_size_t),
     "dcrf_qp_fw": ([_P, _P, _P, _I, _P, _I, _I, _P, _P, _I, _P], _I),
     "dcrf_dc_cccp": ([_P, _P, _P, _I, _P, _I, _I, _I, _P, _P, _I, _P], _I),
+    "dcrf_dc_cccp_trace": ([_P, _P, _P, _I, _P, _I, _I, _I, _P, _P, _P, _I, _P], _I),
     "dcrf_dc_neg": ([_P, _P, _P, _I, _P, _I, _I, _I, _P, _P, _I, _P], _I),
     "dcrf_mean_field": ([_P, _P, _P, _I, _P, _I, _I, _P, _P, _I, _P], _I),
     "dcrf_round": ([_P, ctypes.c_int64, _I, _P, _P, _P], _I),
@@ -351,6 +352,23 @@ def dcrf_dc_cccp(unaries, lattices, weights, Y, outer: int, inner: int, compat=N
                               None if qe is None else qe.ctypes.data_as(_P), STORAGE[storage],
                               _stream(stream)), "dcrf_dc_cccp")
     return None if qe is None else qe.reshape(outer + 1, batch)
+
+
+def dcrf_dc_cccp_trace(unaries, lattices, weights, Y, outer: int, inner: int, compat=None, storage="f32",
+                       stream=None):
+    """dcrf_dc_cccp that also returns the decisions: (S_QP [outer+1, batch],
+    s_trace uint8 [outer * inner, N] on the device)."""
+    unaries = _dev(unaries, torch.float32, "unaries", 2)
+    Y = _dev(Y, torch.float32, "Y", 2)
+    L = unaries.shape[1]
+    batch = lattices[0].batch
+    qe = np.zeros((outer + 1) * batch, dtype=np.float64)
+    trace = torch.empty((outer * inner, Y.shape[0]), dtype=torch.uint8, device=Y.device)
+    cm = _compat(compat, L)
+    _check(lib().dcrf_dc_cccp_trace(_ptr(unaries), _handles(lattices), _floats(weights), len(lattices),
+                                    None if cm is None else cm[1], L, outer, inner, _ptr(Y), qe.ctypes.data_as(_P),
+                                    _ptr(trace), STORAGE[storage], _stream(stream)), "dcrf_dc_cccp_trace")
+    return qe.reshape(outer + 1, batch), trace
 
 
 def dcrf_dc_neg(unaries, lattices, weights, Y, outer: int, inner: int, compat=None, storage="f32",

@@ -1358,14 +1358,19 @@ extern "C" dcrf_status dcrf_qp_fw(const float *unaries, const dcrf_lattice *latt
                             stream);
 }
 
-extern "C" dcrf_status dcrf_dc_cccp(const float *unaries, const dcrf_lattice *lattices, const float *weights,
-                                    int n_kernels, const float *compat, int L, int outer, int inner, float *Y,
-                                    double *qp_energy, int storage, dcrf_stream stream) {
+extern "C" dcrf_status dcrf_dc_cccp_trace(const float *unaries, const dcrf_lattice *lattices, const float *weights,
+                                          int n_kernels, const float *compat, int L, int outer, int inner, float *Y,
+                                          double *qp_energy, uint8_t *s_trace, int storage, dcrf_stream stream) {
     if (outer < 0 || inner < 0) return DCRF_E_INVAL;
     cudaStream_t s = (cudaStream_t)stream;
     Solver S(s);
     DCRF_CHECK_STATUS(S.setup(unaries, lattices, weights, n_kernels, compat, L, storage, Y, outer * inner));
     if (S.n == 0) return DCRF_OK;
+    // row o * inner + i: the decision of inner iteration i of outer step o
+    // (each outer step's start pass rewrites the row the previous step's last
+    // pass wrote, with the new linear term)
+    S.trace = s_trace;
+    S.trace_rows = outer * inner;
     double *qe;
     DCRF_CHECK_STATUS(S.sc.get(&qe, (size_t)(outer + 1) * S.batch));
     // S_QP at y^0
@@ -1395,6 +1400,13 @@ extern "C" dcrf_status dcrf_dc_cccp(const float *unaries, const dcrf_lattice *la
         if (h != 0) return (dcrf_status)h;
     }
     return DCRF_OK;
+}
+
+extern "C" dcrf_status dcrf_dc_cccp(const float *unaries, const dcrf_lattice *lattices, const float *weights,
+                                    int n_kernels, const float *compat, int L, int outer, int inner, float *Y,
+                                    double *qp_energy, int storage, dcrf_stream stream) {
+    return dcrf_dc_cccp_trace(unaries, lattices, weights, n_kernels, compat, L, outer, inner, Y, qp_energy, nullptr,
+                              storage, stream);
 }
 
 namespace {

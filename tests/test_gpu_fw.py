@@ -114,6 +114,39 @@ def test_cccp_medium(dcrf):
     assert abs(c.s_qp(yg) - e[-1]) <= ENERGY_TOL * scale
 
 
+def test_cccp_medium_elementwise(dcrf):
+    # C2: QP Frank-Wolfe (50 iterations) then CCCP 10 x 50 at 320x213, L=21,
+    # FP32.  The oracle replays the GPU's decisions of both phases (each an
+    # argmin of the FP64 gradient up to the FP32 filter tolerance: see
+    # tests/test_gpu_fw_parity.py), and S_QP after every outer step and the
+    # final y are compared element by element.
+    p = S.qp_cccp_medium()
+    g = gpu_setup(dcrf, [p], torch)
+    Y = g["y0"].clone()
+    _, tq = dcrf.dcrf_qp_fw_trace(g["phi"], [g["lb"], g["ls"]], p.weights, Y, 50)
+    yq = Y.cpu().numpy()
+    e, tc = dcrf.dcrf_dc_cccp_trace(g["phi"], [g["lb"], g["ls"]], p.weights, Y, 10, 50)
+    c = oracle_crf(p)
+    bound = 4.0 * 1e-4 * float((c.c_raw + c.kernel.sum_w).max())
+    rows = np.arange(c.n)
+    worst = [0.0]
+
+    def on_step(t, gr, s):
+        worst[0] = max(worst[0], float((gr[rows, s] - gr.min(axis=1)).max()))
+
+    y_o, _, _ = qp.frank_wolfe(c, p.y0, 50, decisions=tq.cpu().numpy().astype(np.int64), on_step=on_step)
+    assert np.abs(yq - y_o).max() <= 1e-3
+    y_c, e_o = qp.cccp_dc_gen(c, yq.astype(np.float64), 10, 50, decisions=tc.cpu().numpy().astype(np.int64),
+                              on_step=on_step)
+    scale = np.abs(e_o).max()
+    print(f"\nCCCP 320x213: energies {np.abs(e[:, 0] - e_o).max() / scale:.3g}, "
+          f"y {np.abs(Y.cpu().numpy() - y_c).max():.3g}, excess/bound {worst[0] / bound:.3g}")
+    assert worst[0] <= bound
+    assert np.abs(e[:, 0] - e_o).max() <= ENERGY_TOL * scale
+    assert np.all(np.diff(e[:, 0]) <= 1e-5 * scale)                # monotone (Section 5.1)
+    assert np.abs(Y.cpu().numpy() - y_c).max() <= 1e-3
+
+
 def test_fw_graph_path_matches_eager(dcrf):
     # a non-default stream takes the captured two-iteration graph path
     p = S.make_problem(64, 48, 5, 5, seed=12)

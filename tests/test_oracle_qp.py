@@ -134,3 +134,15 @@ def test_replayed_decisions_follow_the_definitions():
         assert rec3[t, 2] == qp.step_size(rec3[t, 3], rec3[t, 4])
         y = y + rec3[t, 2] * (s - y)
     np.testing.assert_allclose(y3, y, rtol=1e-12, atol=1e-14)
+
+
+def test_cccp_replayed_decisions_reproduce_the_run():
+    # CCCP (Algorithm 2) with every inner Frank-Wolfe run replaying given
+    # vertices: its own decisions give back the free run exactly
+    c, y0 = _brute_problem(6, n=20, L=4)
+    own = []
+    y1, e1 = qp.cccp_dc_gen(c, y0, 3, 5, on_step=lambda t, g, s: own.append(np.array(s)))
+    assert len(own) == 15
+    y2, e2 = qp.cccp_dc_gen(c, y0, 3, 5, decisions=own)
+    np.testing.assert_array_equal(y1, y2)
+    np.testing.assert_array_equal(e1, e2)
