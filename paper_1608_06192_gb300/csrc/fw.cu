@@ -895,8 +895,6 @@ struct Solver {
         A.y16 = (reinterpret_cast<uintptr_t>(Y) & 15) == 0;
         A.cpart = cpart;
         A.status = status;
-        A.nchunks = n_chunks_pb[q];
-        A.ahead = 1;
         const size_t shm = 2 * (size_t)PB * Ls * sizeof(float);
         void (*kern)(PixArgs, FwLats);
         int threads = PB;
@@ -912,13 +910,6 @@ struct Solver {
         if ((int)shm > attr_shm) {
             DCRF_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
             attr_shm = (int)shm;
-        }
-        if constexpr ((MODE & kPref) != 0) {
-            int dev = 0, sms = 1, per_sm = 1;
-            if (cudaGetDevice(&dev) == cudaSuccess &&
-                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, shm) == cudaSuccess)
-                A.ahead = std::max(1, sms * per_sm);
         }
         if (n_chunks_pb[q] > 0) {
             ProfScope ps(P_FW_PIXEL, s);
@@ -954,8 +945,6 @@ struct Solver {
                 DCRF_PIX_CASE(16);
                 DCRF_PIX_CASE(17);
                 DCRF_PIX_CASE(18);
-                DCRF_PIX_CASE(19);
-                DCRF_PIX_CASE(20);
             default: return pixel_v<LPc, T, POT, kPixPB[0], kPixMB[0], kPixMode[0]>(Y, phi, start, al);
             }
 #undef DCRF_PIX_CASE

@@ -24,15 +24,11 @@ namespace {
 // kL21 fixes L = 21 at compile time (the label count of the segmentation
 // workloads): the loops over the padded 24 labels lose their runtime bounds
 // and the padding labels' accumulators and FMAs go away.
-// kPref: at its start a block asks L2 to prefetch (bulk prefetch, one
-// instruction per array) the y and lin tiles and the simplex tables of the
-// chunk that will run on its SM one wave later (blockIdx + the resident grid),
-// so that the next block's dependent index loads hit L2 instead of DRAM.
-constexpr int kFix = 1, kF2 = 2, kL3 = 4, kEarly = 8, kBulk = 16, kLean = 32, kL21 = 64, kPref = 128;
-constexpr int kPixVariants = 21;
+constexpr int kFix = 1, kF2 = 2, kL3 = 4, kEarly = 8, kBulk = 16, kLean = 32, kL21 = 64;
+constexpr int kPixVariants = 19;
 constexpr int kPixPB[kPixVariants] = {256, 128, 256, 128, 256, 80, 128, 256, 128, 128,
-                                      128, 128, 128, 128, 128, 128, 128, 128, 128, 128, 128};
-constexpr int kPixMB[kPixVariants] = {4, 8, 3, 6, 3, 0, 6, 3, 6, 8, 7, 8, 7, 6, 7, 8, 7, 8, 6, 7, 8};
+                                      128, 128, 128, 128, 128, 128, 128, 128, 128};
+constexpr int kPixMB[kPixVariants] = {4, 8, 3, 6, 3, 0, 6, 3, 6, 8, 7, 8, 7, 6, 7, 8, 7, 8, 6};
 constexpr int kPixMode[kPixVariants] = {0,           0,           kFix,         kFix,
                                         kFix | kF2,  kL3,         kFix | kEarly, kFix | kEarly,
                                         kFix | kF2 | kEarly, kFix | kEarly, kFix | kF2 | kEarly,
@@ -41,9 +37,7 @@ constexpr int kPixMode[kPixVariants] = {0,           0,           kFix,         
                                         kFix | kF2 | kEarly | kBulk | kLean,
                                         kFix | kF2 | kEarly | kBulk | kLean | kL21,
                                         kFix | kF2 | kEarly | kBulk | kLean | kL21,
-                                        kFix | kF2 | kEarly | kBulk | kLean | kL21,
-                                        kFix | kF2 | kEarly | kBulk | kLean | kL21 | kPref,
-                                        kFix | kF2 | kEarly | kBulk | kLean | kL21 | kPref};
+                                        kFix | kF2 | kEarly | kBulk | kLean | kL21};
 // whether variant v can run a problem with L labels
 constexpr bool pixel_variant_fits(int v, int L) { return (kPixMode[v] & kL21) == 0 || L == 21; }
 // chunk list of a pixel-block size (256, 128 or 80 pixels)
@@ -154,8 +148,6 @@ struct PixArgs {
     bool y16;              // Y starts on a 16-byte boundary (lin always does)
     float *cpart;          // [chunks][PB / 32][NS] per-warp sums
     int *status;
-    int nchunks;           // chunks of the launch
-    int ahead;             // blocks resident at once (the prefetch distance of kPref)
 };
 
 template <typename TB>
@@ -254,15 +246,6 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, long long pol
         if (done) return true;
     }
     return false;
-}
-// asks L2 to fetch [p, p + bytes) (p and bytes multiples of 16)
-__device__ __forceinline__ void bulk_prefetch_l2(const void *p, unsigned bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void prefetch_l2_range(const void *p, size_t bytes) {
-    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
-    const uintptr_t b = (a + 15) & ~(uintptr_t)15, e = (a + bytes) & ~(uintptr_t)15;
-    if (e > b) bulk_prefetch_l2(reinterpret_cast<const void *>(b), (unsigned)(e - b));
 }
 // shared -> global bulk store of this thread; returns after the shared source was read
 __device__ __forceinline__ void bulk_s2g(void *dst, const void *src, unsigned bytes) {
@@ -801,26 +784,6 @@ __global__ void __launch_bounds__(PB, MB) k_fw_pixel(PixArgs A, FwLats F) {
     if constexpr ((MODE & kBulk) != 0) {
         static_assert((MODE & kEarly) != 0, "bulk tiles wait in the early-gather path");
         if (tile_bulk_ok(A, ch)) tbar = &tbar_s;     // uniform over the block
-    }
-    if constexpr ((MODE & kPref) != 0) {
-        const int nb = blockIdx.x + A.ahead;
-        if (nb < A.nchunks && threadIdx.x < 6) {
-            const Chunk cn = A.chunks[nb];
-            const size_t rows = (size_t)cn.count * A.L * sizeof(float);
-            switch (threadIdx.x) {
-            case 0: prefetch_l2_range(A.Y + cn.begin * (int64_t)A.L, rows); break;
-            case 1: prefetch_l2_range(A.lin + cn.begin * (int64_t)A.L, rows); break;
-            default: {
-                const int m = (threadIdx.x - 2) >> 1;
-                if (m < F.nk) {
-                    const FwLat &lt = F.l[m];
-                    const size_t cnt = (size_t)cn.count * lt.d1 * 4;
-                    if ((threadIdx.x & 1) == 0) prefetch_l2_range(lt.pvid + cn.begin * lt.d1, cnt);
-                    else prefetch_l2_range(lt.pbary + cn.begin * lt.d1, cnt);
-                }
-            }
-            }
-        }
     }
     if (tbar) {
         if (threadIdx.x == 0) mbar_init(tbar);
