@@ -159,6 +159,11 @@ dcrf_status dcrf_slice_f32(const dcrf_lattice lat, const float *V, int Lp, int L
 // the result lands in kout/vout, ktmp/vtmp are scratch, kin/vin are read only.
 dcrf_status dcrf_segsort(const uint32_t *kin, const int32_t *vin, uint32_t *ktmp, int32_t *vtmp, uint32_t *kout,
                          int32_t *vout, const int64_t *seg_begin, int nseg, int bits, cudaStream_t s);
+// Prefix sums of integer arrays (scan.cu): out[i] = sum of in[0 .. i)
+// (exclusive) or in[0 .. i] (inclusive); out may not alias in.
+dcrf_status dcrf_scan(const int32_t *in, int32_t *out, int64_t n, bool inclusive, cudaStream_t s);
+dcrf_status dcrf_scan(const uint32_t *in, int64_t *out, int64_t n, bool inclusive, cudaStream_t s);
+dcrf_status dcrf_scan(const int32_t *in, int64_t *out, int64_t n, bool inclusive, cudaStream_t s);
 // Looks up, once per device, the device address of dcrf_filter_static's
 // array for the device of stream s (noalloc.cu).
 dcrf_status dcrf_static_scratch(cudaStream_t s, unsigned char **out);

@@ -9,8 +9,6 @@
 //   m_i   = rint(x_i / (d+1)), rank correction, barycentric weights
 //   blur  = d+1 Jacobi passes [1/4, 1/2, 1/4] along w_j = (d+1) e_j - 1
 //   s0    = (2 pi)^{d/2} alpha^d / (d+1)^{d - 1/2}
-#include <cub/device/device_radix_sort.cuh>
-#include <cub/device/device_scan.cuh>
 
 #include <algorithm>
 #include <cmath>
@@ -274,7 +272,11 @@ __global__ void k_embed_insert(const float *__restrict__ feat, int64_t n, EmbedP
 // Vertex numbering by first touch: first[slot] = the lowest incidence index
 // a (d+1) + k that lands on the slot.  Vertices are then numbered in that
 // order, so pixels that are close in raster order find their corners close
-// in memory (and the numbering no longer depends on the hash layout).
+// in memory (and the numbering no longer depends on the hash layout).  The
+// first-touch indices of distinct vertices are distinct, so a vertex's number
+// is the count of vertices first touched at a lower incidence index: mark the
+// first touches, take an exclusive prefix sum over the incidences, and read it
+// at each vertex's own first touch.
 __global__ void k_first_touch(const int64_t *__restrict__ pslot, int64_t count,
                               unsigned long long *__restrict__ first) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -283,25 +285,16 @@ __global__ void k_first_touch(const int64_t *__restrict__ pslot, int64_t count,
     if (slot >= 0 && first[slot] > (unsigned long long)i) atomicMin(first + slot, (unsigned long long)i);
 }
 
-__global__ void k_vertex_first(const unsigned long long *__restrict__ first, int64_t slots,
-                               const int32_t *__restrict__ flag, const int32_t *__restrict__ scan,
-                               unsigned long long *__restrict__ vkey, int32_t *__restrict__ vold) {
+__global__ void k_mark_first(const unsigned long long *__restrict__ first, int64_t slots,
+                             const int32_t *__restrict__ flag, int32_t *__restrict__ mark) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= slots || !flag[i]) return;
-    const int v = scan[i];
-    vkey[v] = first[i];
-    vold[v] = v;
+    if (i < slots && flag[i]) mark[first[i]] = 1;
 }
 
-__global__ void k_rank_of(const int32_t *__restrict__ vold_sorted, int64_t m, int32_t *__restrict__ rank) {
-    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (r < m) rank[vold_sorted[r]] = (int32_t)r;
-}
-
-__global__ void k_slot_ids(const int32_t *__restrict__ flag, const int32_t *__restrict__ scan,
-                           const int32_t *__restrict__ rank, int64_t slots, int32_t *__restrict__ ids) {
+__global__ void k_slot_ids(const unsigned long long *__restrict__ first, const int32_t *__restrict__ flag,
+                           const int32_t *__restrict__ before, int64_t slots, int32_t *__restrict__ ids) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < slots) ids[i] = flag[i] ? rank[scan[i]] : 0;
+    if (i < slots) ids[i] = flag[i] ? before[first[i]] : 0;
 }
 
 __global__ void k_occupied(const unsigned long long *__restrict__ table, int64_t slots,
@@ -690,11 +683,7 @@ static dcrf_status build_typed(dcrf_lattice lat, const float *feat, cudaStream_t
     }
     k_occupied<<<blocks_for(slots, 256), 256, 0, s>>>(table, slots, flag);
     DCRF_LAUNCHED();
-    size_t tmp_bytes = 0;
-    DCRF_TRY(cub::DeviceScan::ExclusiveSum(nullptr, tmp_bytes, flag, scan, (int)slots, s));
-    void *tmp;
-    DCRF_CHECK_STATUS(sc.get((char **)&tmp, tmp_bytes));
-    DCRF_TRY(cub::DeviceScan::ExclusiveSum(tmp, tmp_bytes, flag, scan, (int)slots, s));
+    DCRF_CHECK_STATUS(dcrf_scan(flag, scan, slots, false, s));
     k_vertex_offsets<<<1, 1024, 0, s>>>(scan, flag, base_d, batch, slots, lat->vert_off_d);
     DCRF_LAUNCHED();
     lat->vert_off.assign(batch + 1, 0);
@@ -708,31 +697,20 @@ static dcrf_status build_typed(dcrf_lattice lat, const float *feat, cudaStream_t
     // vertex of image b is first touched by a point of image b)
     int32_t *ids = scan;
     if (m > 1) {
-        unsigned long long *first, *vkey, *vkey2;
-        int32_t *vold, *vold2, *rank;
+        unsigned long long *first;
+        int32_t *mark, *before;
         DCRF_CHECK_STATUS(sc.get(&first, slots));
-        DCRF_CHECK_STATUS(sc.get(&vkey, m));
-        DCRF_CHECK_STATUS(sc.get(&vkey2, m));
-        DCRF_CHECK_STATUS(sc.get(&vold, m));
-        DCRF_CHECK_STATUS(sc.get(&vold2, m));
-        DCRF_CHECK_STATUS(sc.get(&rank, m));
+        DCRF_CHECK_STATUS(sc.get(&mark, (size_t)n * D1));
+        DCRF_CHECK_STATUS(sc.get(&before, (size_t)n * D1));
         DCRF_CHECK_STATUS(sc.get(&ids, slots));
         DCRF_TRY(cudaMemsetAsync(first, 0xFF, slots * sizeof(unsigned long long), s));
+        DCRF_TRY(cudaMemsetAsync(mark, 0, (size_t)n * D1 * sizeof(int32_t), s));
         k_first_touch<<<blocks_for(n * D1, 256), 256, 0, s>>>(pslot, n * D1, first);
         DCRF_LAUNCHED();
-        k_vertex_first<<<blocks_for(slots, 256), 256, 0, s>>>(first, slots, flag, scan, vkey, vold);
+        k_mark_first<<<blocks_for(slots, 256), 256, 0, s>>>(first, slots, flag, mark);
         DCRF_LAUNCHED();
-        int end_bit = 1;
-        while (end_bit < 64 && ((unsigned long long)(n * D1) >> end_bit) != 0) ++end_bit;
-        size_t sort_bytes = 0;
-        DCRF_TRY(cub::DeviceRadixSort::SortPairs(nullptr, sort_bytes, vkey, vkey2, vold, vold2, (int)m, 0, end_bit, s));
-        char *sort_tmp;
-        DCRF_CHECK_STATUS(sc.get(&sort_tmp, sort_bytes));
-        DCRF_TRY(cub::DeviceRadixSort::SortPairs(sort_tmp, sort_bytes, vkey, vkey2, vold, vold2, (int)m, 0, end_bit,
-                                                 s));
-        k_rank_of<<<blocks_for(m, 256), 256, 0, s>>>(vold2, m, rank);
-        DCRF_LAUNCHED();
-        k_slot_ids<<<blocks_for(slots, 256), 256, 0, s>>>(flag, scan, rank, slots, ids);
+        DCRF_CHECK_STATUS(dcrf_scan(mark, before, n * D1, false, s));
+        k_slot_ids<<<blocks_for(slots, 256), 256, 0, s>>>(first, flag, before, slots, ids);
         DCRF_LAUNCHED();
     }
 

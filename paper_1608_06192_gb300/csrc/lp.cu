@@ -16,8 +16,6 @@
 // Per level: splat the right-child indicator into the runs, d+1 Jacobi blur
 // passes over the runs, slice at the left-child points into U.
 // Finally G = phi + 2U - c and S_LP = <y, G>.
-#include <cub/device/device_radix_sort.cuh>
-#include <cub/device/device_scan.cuh>
 #include <cub/device/device_segmented_radix_sort.cuh>
 
 #include <algorithm>
@@ -746,17 +744,17 @@ struct LpWork {
         int dmax = 1;
         for (int m = 0; m < nk; ++m) dmax = std::max(dmax, lattices[m]->d + 1);
         DCRF_CHECK_STATUS(sc.get(&rnbr, ne * dmax * 2));
-        // temp storage for the sorts and scans
-        size_t t1 = 0, t2 = 0, t3 = 0;
-        DCRF_TRY(cub::DeviceSegmentedRadixSort::SortPairs(nullptr, t1, keys, keys2, vals, perm, (int)nl, C * batch,
-                                                          seg_b, seg_e, 0, 32, s));
-        DCRF_TRY(cub::DeviceSegmentedRadixSort::SortPairs(nullptr, t2, ekey, ekey2, eq, eq2, (int)ne, C * batch,
-                                                          eseg_b, eseg_e, 0, 32, s));
-        DCRF_TRY(cub::DeviceScan::InclusiveSum(nullptr, t3, flag, rid, (int)ne, s));
-        tmp_bytes = std::max(t1, std::max(t2, t3));
-        char *t;
-        DCRF_CHECK_STATUS(sc.get(&t, tmp_bytes));
-        tmp = t;
+        if (cub_sort) {   // temp storage for the CUB sorts (the comparator path)
+            size_t t1 = 0, t2 = 0;
+            DCRF_TRY(cub::DeviceSegmentedRadixSort::SortPairs(nullptr, t1, keys, keys2, vals, perm, (int)nl,
+                                                              C * batch, seg_b, seg_e, 0, 32, s));
+            DCRF_TRY(cub::DeviceSegmentedRadixSort::SortPairs(nullptr, t2, ekey, ekey2, eq, eq2, (int)ne, C * batch,
+                                                              eseg_b, eseg_e, 0, 32, s));
+            tmp_bytes = std::max(t1, t2);
+            char *t;
+            DCRF_CHECK_STATUS(sc.get(&t, tmp_bytes));
+            tmp = t;
+        }
         // incidence offsets per vertex (label independent)
         for (int m = 0; m < nk; ++m) {
             const dcrf_lattice lat = lattices[m];
@@ -768,11 +766,7 @@ struct LpWork {
                 k_lp_csr_count<<<nb(n * (lat->d + 1), 256), 256, 0, s>>>(lat->pvid, n * (lat->d + 1), cnt);
                 DCRF_LAUNCHED();
             }
-            size_t tb = 0;
-            DCRF_TRY(cub::DeviceScan::ExclusiveSum(nullptr, tb, cnt, csr[m], (int)(lat->m + 1), s));
-            char *tt;
-            DCRF_CHECK_STATUS(sc.get(&tt, tb));
-            DCRF_TRY(cub::DeviceScan::ExclusiveSum(tt, tb, cnt, csr[m], (int)(lat->m + 1), s));
+            DCRF_CHECK_STATUS(dcrf_scan(cnt, csr[m], lat->m + 1, false, s));
         }
         // c_a
         const float *ones_h[DCRF_MAX_KERNELS];
@@ -901,8 +895,7 @@ struct LpWork {
                     ProfScope ps(P_LP_RUNS, s);
                     k_lp_flags<<<nb(E, 256), 256, 0, s>>>(A, flag);
                     DCRF_LAUNCHED();
-                    size_t tb = tmp_bytes;
-                    DCRF_TRY(cub::DeviceScan::InclusiveSum(tmp, tb, flag, rid, (int)E, s));
+                    DCRF_CHECK_STATUS(dcrf_scan(flag, rid, E, true, s));
                 }
                 // rid[e] = 1 + run of entry e; the number of runs is rid[E-1]
                 int32_t last = 0;
