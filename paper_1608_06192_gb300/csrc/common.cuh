@@ -159,6 +159,13 @@ dcrf_status dcrf_slice_f32(const dcrf_lattice lat, const float *V, int Lp, int L
 // the result lands in kout/vout, ktmp/vtmp are scratch, kin/vin are read only.
 dcrf_status dcrf_segsort(const uint32_t *kin, const int32_t *vin, uint32_t *ktmp, int32_t *vtmp, uint32_t *kout,
                          int32_t *vout, const int64_t *seg_begin, int nseg, int bits, cudaStream_t s);
+// idx / cols for 0 <= idx < count: the 32-bit division when count fits 32
+// bits (a branch that is uniform over the launch), else the 64-bit one, whose
+// long instruction sequence dominated the element-wise kernels that index
+// [rows][cols] arrays by a flat index.
+__device__ __forceinline__ int64_t dcrf_div(int64_t idx, int cols, int64_t count) {
+    return count <= 0xffffffffll ? (int64_t)((uint32_t)idx / (uint32_t)cols) : idx / cols;
+}
 // Prefix sums of integer arrays (scan.cu): out[i] = sum of in[0 .. i)
 // (exclusive) or in[0 .. i] (inclusive); out may not alias in.
 dcrf_status dcrf_scan(const int32_t *in, int32_t *out, int64_t n, bool inclusive, cudaStream_t s);

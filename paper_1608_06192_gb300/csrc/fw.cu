@@ -473,11 +473,18 @@ __device__ __forceinline__ void pixel_sums(const PartSums &P, int b, double (&sg
     image_sums<NS>(P.cpart, P.crange[b], P.crange[b + 1], sg);
 }
 
-// Step size and record of one iteration, one block per image; the last block
-// to finish advances the iteration counter.
-__global__ void __launch_bounds__(1024) k_fw_alpha(PartSums P, double *alpha, dcrf_fw_record *rec, int *counter, int *ticket,
-                           int *status) {
-    const int b = blockIdx.x;
+// Step size and record of one iteration.  kAlphaSplit blocks per image each
+// reduce a share of the image's partial rows (compensated FP32, then FP64 as
+// hi + lo); the last of them to finish adds the shares in FP64 in block order
+// (so the result does not depend on which block finishes last) and writes
+// alpha and the record; the last image to finish advances the iteration
+// counter.  One block per image left each block with several dependent
+// rounds of loads: the kernel took ~15 us at any batch size.
+constexpr int kAlphaSplit = 4;
+
+__global__ void __launch_bounds__(1024) k_fw_alpha(PartSums P, double *alpha, dcrf_fw_record *rec, int *counter,
+                                                   int *ticket, int *img_ticket, double *share, int *status) {
+    const int b = blockIdx.x / kAlphaSplit, j = blockIdx.x - b * kAlphaSplit;
     const int t = *counter;
     // one pass: the pixel sums in columns 0 .. NS-1, the lattice dot products
     // of every lattice in columns NS, NS+1 (they only enter as their total)
@@ -485,43 +492,62 @@ __global__ void __launch_bounds__(1024) k_fw_alpha(PartSums P, double *alpha, dc
     float hi[T], lo[T];
 #pragma unroll
     for (int q = 0; q < T; ++q) hi[q] = lo[q] = 0.f;
-    rows_into<NS, 0, T>(P.cpart, P.crange[b], P.crange[b + 1], hi, lo);
+    // share j of rows [r0, r1)
+    auto lo_of = [j](int r0, int r1) { return r0 + (int)((int64_t)(r1 - r0) * j / kAlphaSplit); };
+    auto hi_of = [j](int r0, int r1) { return r0 + (int)((int64_t)(r1 - r0) * (j + 1) / kAlphaSplit); };
+    {
+        const int r0 = P.crange[b], r1 = P.crange[b + 1];
+        rows_into<NS, 0, T>(P.cpart, lo_of(r0, r1), hi_of(r0, r1), hi, lo);
+    }
 #pragma unroll
     for (int m = 0; m < DCRF_MAX_KERNELS; ++m) {
         if (m >= P.nk) break;
         const int *vr = P.vrange + m * (P.batch + 1);
-        rows_into<2, NS, T>(P.vpart, vr[b], vr[b + 1], hi, lo);
+        rows_into<2, NS, T>(P.vpart, lo_of(vr[b], vr[b + 1]), hi_of(vr[b], vr[b + 1]), hi, lo);
     }
     double sg[T];
     block_sums<T>(hi, lo, sg);
+    if (threadIdx.x != 0) return;
+    double *mine = share + (int64_t)blockIdx.x * T;
+#pragma unroll
+    for (int q = 0; q < T; ++q) mine[q] = sg[q];
+    __threadfence();
+    if (atomicAdd(img_ticket + b, 1) != kAlphaSplit - 1) return;
+    img_ticket[b] = 0;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < T; ++q) sg[q] = 0.0;
+    for (int k = 0; k < kAlphaSplit; ++k) {
+        const double *sh = share + ((int64_t)b * kAlphaSplit + k) * T;
+#pragma unroll
+        for (int q = 0; q < T; ++q) sg[q] += __ldcg(sh + q);
+    }
     const double yPs = sg[4] + sg[NS], sPs = sg[5] + sg[NS + 1];
-    if (threadIdx.x == 0) {
-        const double A = sPs - sg[3] - yPs + sg[1];
-        const double B = sg[2] - sg[0] + yPs - 2.0 * sg[1] + sg[3];
-        double al;
-        if (!isfinite(A) || !isfinite(B)) {
-            dcrf_flag(status, DCRF_E_NONFINITE);
-            al = 0.0;
-        } else if (A > 0.0) {
-            al = fmin(1.0, fmax(0.0, -B / (2.0 * A)));
-        } else {
-            al = (A + B < 0.0) ? 1.0 : 0.0;
-        }
-        alpha[b] = al;
-        if (rec) {
-            dcrf_fw_record r;
-            r.energy = sg[0] + sg[1];
-            r.gap = sg[0] + 2.0 * sg[1] - sg[2] - 2.0 * sg[3];
-            r.alpha = al;
-            r.A = A;
-            r.B = B;
-            rec[(int64_t)t * P.batch + b] = r;
-        }
-        __threadfence();
-        if (atomicAdd(ticket, 1) == (int)gridDim.x - 1) {
-            *ticket = 0;
-            *counter = t + 1;
-        }
+    const double A = sPs - sg[3] - yPs + sg[1];
+    const double B = sg[2] - sg[0] + yPs - 2.0 * sg[1] + sg[3];
+    double al;
+    if (!isfinite(A) || !isfinite(B)) {
+        dcrf_flag(status, DCRF_E_NONFINITE);
+        al = 0.0;
+    } else if (A > 0.0) {
+        al = fmin(1.0, fmax(0.0, -B / (2.0 * A)));
+    } else {
+        al = (A + B < 0.0) ? 1.0 : 0.0;
+    }
+    alpha[b] = al;
+    if (rec) {
+        dcrf_fw_record r;
+        r.energy = sg[0] + sg[1];
+        r.gap = sg[0] + 2.0 * sg[1] - sg[2] - 2.0 * sg[3];
+        r.alpha = al;
+        r.A = A;
+        r.B = B;
+        rec[(int64_t)t * P.batch + b] = r;
+    }
+    __threadfence();
+    if (atomicAdd(ticket, 1) == P.batch - 1) {
+        *ticket = 0;
+        *counter = t + 1;
     }
 }
 
@@ -600,7 +626,7 @@ __global__ void k_fw_splat_y0(const float *__restrict__ Y, int64_t n, int L, int
     const int H = Lp >> 1;
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= n * H) return;
-    const int64_t a = idx / H;
+    const int64_t a = dcrf_div(idx, H, n * H);
     const int c0 = 2 * (int)(idx - a * H);
     const float q = __ldg(qs);
     const float y0 = c0 < L ? fmaxf(Y[a * L + c0], 0.f) : 0.f;
@@ -637,17 +663,51 @@ __global__ void k_fw_c(int64_t n, FwLats F, const float *const *ones, const floa
     c[a] = s > 0.f ? s : 0.f;
 }
 
-__global__ void k_fw_lin(int64_t n, int L, const float *phi, const float *c, const float *musum,
-                         const float *Y, float scale, float *lin, int *status) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n * L) return;
-    const int64_t a = i / L;
-    const int l = (int)(i - a * L);
-    const float p = phi[i];
+// lin = phi - scale musum o c y (y = 1 when Y is null), eight consecutive
+// elements of the flat [n][L] arrays per thread: two 16-byte loads of phi
+// (and of Y) when the arrays are 16-byte aligned, else eight scalar ones
+// (one thread per element kept too few bytes in flight to reach HBM speed).
+__device__ __forceinline__ float fw_lin_one(float p, float yv, float scale, const float *musum, const float *c,
+                                            int64_t a, int l, int *status) {
     if (!isfinite(p)) dcrf_flag(status, DCRF_E_NONFINITE);
-    const float yv = Y ? Y[i] : 1.f;
-    lin[i] = p - scale * musum[l] * c[a] * yv;
+    return p - scale * musum[l] * c[a] * yv;
 }
+
+__global__ void k_fw_lin(int64_t n, int L, const float *phi, const float *c, const float *musum,
+                         const float *Y, float scale, float *lin, int *status, bool vec) {
+    const int64_t count = n * L;
+    const int64_t i0 = 8 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+    if (i0 >= count) return;
+    int64_t a = dcrf_div(i0, L, count);
+    int l = (int)(i0 - a * L);
+    if (vec && i0 + 8 <= count) {
+        float p[8], yv[8], o[8];
+        const float4 p0 = reinterpret_cast<const float4 *>(phi + i0)[0], p1 = reinterpret_cast<const float4 *>(phi + i0)[1];
+        p[0] = p0.x; p[1] = p0.y; p[2] = p0.z; p[3] = p0.w; p[4] = p1.x; p[5] = p1.y; p[6] = p1.z; p[7] = p1.w;
+        if (Y) {
+            const float4 y0 = reinterpret_cast<const float4 *>(Y + i0)[0], y1 = reinterpret_cast<const float4 *>(Y + i0)[1];
+            yv[0] = y0.x; yv[1] = y0.y; yv[2] = y0.z; yv[3] = y0.w; yv[4] = y1.x; yv[5] = y1.y; yv[6] = y1.z; yv[7] = y1.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) yv[j] = 1.f;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            o[j] = fw_lin_one(p[j], yv[j], scale, musum, c, a, l, status);
+            if (++l == L) { l = 0; ++a; }
+        }
+        reinterpret_cast<float4 *>(lin + i0)[0] = make_float4(o[0], o[1], o[2], o[3]);
+        reinterpret_cast<float4 *>(lin + i0)[1] = make_float4(o[4], o[5], o[6], o[7]);
+        return;
+    }
+    const int64_t i1 = i0 + 8 < count ? i0 + 8 : count;
+    for (int64_t i = i0; i < i1; ++i) {
+        lin[i] = fw_lin_one(phi[i], Y ? Y[i] : 1.f, scale, musum, c, a, l, status);
+        if (++l == L) { l = 0; ++a; }
+    }
+}
+
+inline bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
 __global__ void __launch_bounds__(1024) k_fw_qp_energy(PartSums P, double *out) {
     double sg[NS];
@@ -683,6 +743,8 @@ struct Solver {
     std::vector<int64_t> voff;                 // first vpart warp row of each lattice
     double *alpha = nullptr;
     int *counter = nullptr, *ticket = nullptr;
+    int *img_ticket = nullptr;                 // [batch] blocks of k_fw_alpha done per image
+    double *alpha_share = nullptr;             // [batch][kAlphaSplit][NS + 2] their sums
     dcrf_fw_record *rec = nullptr;
     int *status = nullptr;
     uint8_t *trace = nullptr;                  // [trace_rows][n] decisions s^t, or null
@@ -804,6 +866,9 @@ struct Solver {
         ticket = counter + 1;
         DCRF_CHECK_STATUS(sc.get(&rec, (size_t)batch * (max_records > 0 ? max_records : 1)));
         DCRF_TRY(cudaMemsetAsync(counter, 0, 2 * sizeof(int), s));
+        DCRF_CHECK_STATUS(sc.get(&img_ticket, (size_t)batch));
+        DCRF_CHECK_STATUS(sc.get(&alpha_share, (size_t)batch * kAlphaSplit * (NS + 2)));
+        DCRF_TRY(cudaMemsetAsync(img_ticket, 0, batch * sizeof(int), s));
         // c_a and lin = phi - d
         const float *ones_h[DCRF_MAX_KERNELS];
         for (int m = 0; m < nk; ++m) ones_h[m] = lattices[m]->ones;
@@ -816,7 +881,8 @@ struct Solver {
         if (n > 0) {
             k_fw_c<<<nblocks(n, 256), 256, 0, s>>>(n, F, ones_d, w_d, nk, sumw, c);
             DCRF_LAUNCHED();
-            k_fw_lin<<<nblocks(n * L, 256), 256, 0, s>>>(n, L, unaries, c, musum, nullptr, 1.f, lin, status);
+            k_fw_lin<<<nblocks((n * L + 7) / 8, 256), 256, 0, s>>>(n, L, unaries, c, musum, nullptr, 1.f, lin, status,
+                                                                   aligned16(unaries) && aligned16(lin));
             DCRF_LAUNCHED();
         }
         // fixed-point scales of the one-hot splats: an entry of S s is at most
@@ -1238,7 +1304,8 @@ struct Solver {
         DCRF_CHECK_STATUS(latdot());
         {
             ProfScope ps(P_FW_ALPHA, s);
-            k_fw_alpha<<<batch, 1024, 0, s>>>(parts(), alpha, rec, counter, ticket, status);
+            k_fw_alpha<<<batch * kAlphaSplit, 1024, 0, s>>>(parts(), alpha, rec, counter, ticket, img_ticket,
+                                                           alpha_share, status);
         }
         DCRF_LAUNCHED();
         UpdArgs U{};
@@ -1381,7 +1448,8 @@ extern "C" dcrf_status dcrf_dc_cccp_trace(const float *unaries, const dcrf_latti
     (void)G;
     for (int o = 0; o < outer; ++o) {
         // linearise q at y^t: lin = phi - 2 d o y^t
-        k_fw_lin<<<nblocks(S.n * L, 256), 256, 0, s>>>(S.n, L, unaries, S.c, S.musum, Y, 2.f, S.lin, S.status);
+        k_fw_lin<<<nblocks((S.n * L + 7) / 8, 256), 256, 0, s>>>(S.n, L, unaries, S.c, S.musum, Y, 2.f, S.lin, S.status,
+                                                                 aligned16(unaries) && aligned16(Y) && aligned16(S.lin));
         DCRF_LAUNCHED();
         for (int m = 0; m < S.nk; ++m)
             DCRF_TRY(cudaMemsetAsync(S.sbuf[m][S.par], 0,

@@ -398,7 +398,7 @@ __global__ void k_blur_pass(const Tin *__restrict__ in, Tout *__restrict__ out,
                             const int32_t *__restrict__ nbr, int64_t m, int G, int j, int D1) {
     int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= m * G) return;
-    int64_t v = idx / G;
+    int64_t v = dcrf_div(idx, G, m * G);
     int g = (int)(idx - v * G);
     int2 nb = reinterpret_cast<const int2 *>(nbr)[v * D1 + j];
     float4 c = load4(in, idx);
@@ -469,7 +469,7 @@ __global__ void k_splat_dense(const float *__restrict__ Y, int64_t n, int L, int
     const int G = Lp >> 2;
     int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= n * G) return;
-    const int64_t a = idx / G;
+    const int64_t a = dcrf_div(idx, G, n * G);
     const int g = (int)(idx - a * G);
     const int c0 = 4 * g;
     float4 y;
@@ -502,7 +502,7 @@ __global__ void k_slice(const T *__restrict__ V, int64_t n, int L, int G, int D1
                         float *__restrict__ out) {
     int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= n * G) return;
-    int64_t a = idx / G;
+    int64_t a = dcrf_div(idx, G, n * G);
     int g = (int)(idx - a * G);
     float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int k = 0; k < D1; ++k) {

@@ -49,7 +49,7 @@ __global__ void k_lp_transpose(const float *__restrict__ Y, int64_t n, int L, ui
                                int32_t *__restrict__ vals, int *status) {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= n * L) return;
-    const int64_t a = q / L;
+    const int64_t a = dcrf_div(q, L, n * L);
     const int i = (int)(q - a * L);
     float v = Y[q];
     if (!isfinite(v)) dcrf_flag(status, DCRF_E_NONFINITE);
@@ -63,7 +63,7 @@ __global__ void k_lp_columns(const float *__restrict__ Y, int64_t n, int L, int 
                              uint32_t *__restrict__ keys, int32_t *__restrict__ vals, int *status) {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= n * C) return;
-    const int64_t a = q / C;
+    const int64_t a = dcrf_div(q, C, n * C);
     const int t = (int)(q - a * C);
     const uint64_t mk = mask[t];
     float v = 0.f;
@@ -88,7 +88,7 @@ __global__ void k_lp_segments(const int64_t *__restrict__ off, int batch, int L,
 __global__ void k_lp_inverse(const int32_t *__restrict__ perm, int64_t n, int L, int32_t *__restrict__ inv) {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= n * L) return;
-    const int64_t i = q / n;
+    const int64_t i = dcrf_div(q, (int)n, n * L);
     inv[i * n + perm[q]] = (int32_t)(q - i * n);
 }
 
@@ -100,9 +100,9 @@ __global__ void k_lp_entries(const int32_t *__restrict__ perm, int64_t n, int L,
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t E = n * L * d1;
     if (q >= E) return;
-    const int64_t ip = q / d1;
+    const int64_t ip = dcrf_div(q, d1, E);
     const int k = (int)(q - ip * d1);
-    const int64_t i = ip / n;
+    const int64_t i = dcrf_div(ip, (int)n, n * L);
     const int32_t a = perm[ip];
     const int v = pvid[(int64_t)a * d1 + k];
     (void)i;
@@ -260,7 +260,7 @@ __global__ void k_lp_combine(const float *__restrict__ phi, const float *__restr
     double part = 0.0;
     int img = -1;
     if (q < n * L) {
-        const int64_t a = q / L;
+        const int64_t a = dcrf_div(q, L, n * L);
         const int i = (int)(q - a * L);
         const float g = phi[q] + 2.f * U[(int64_t)i * n + inv[(int64_t)i * n + a]] - c[a];
         G[q] = g;
@@ -300,7 +300,7 @@ __global__ void k_lp_combine_tree(const float *__restrict__ phi, const float *__
     double part = 0.0;
     int img = -1;
     if (q < n * L) {
-        const int64_t a = q / L;
+        const int64_t a = dcrf_div(q, L, n * L);
         const int k = (int)(q - a * L);
         float g = phi[q];
         for (int t = 0; t < C; ++t)
@@ -982,7 +982,7 @@ __global__ void k_lp_copy_rows(const float *__restrict__ src, float *__restrict_
                                const int64_t *__restrict__ off, int batch, const int *__restrict__ take) {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= n * L) return;
-    const int64_t a = q / L;
+    const int64_t a = dcrf_div(q, L, n * L);
     int lo = 0, hi = batch - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
