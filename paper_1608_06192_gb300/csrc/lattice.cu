@@ -182,16 +182,30 @@ __global__ void k_embed_insert(const float *__restrict__ feat, int64_t n, EmbedP
     }
     x[0] = sm;
 
-    // nearest remainder-0 point
+    // nearest remainder-0 point: m_i = rint(x_i / (d+1)) and
+    // delta_i = x_i - (d+1) m_i, as the correctly rounded quotient gives them,
+    // without the FP64 division where that is provable (FP64 throughput bounds
+    // this kernel).  With k = rint(x RN(1/(d+1))) and rem = RN(x - (d+1) k),
+    // |RN(x/(d+1)) - k| <= |rem|/(d+1) + 2^-53 (|k| + 2), so when
+    // |rem| <= (d+1) (1/2 - 2^-50 (|k| + 2)) the quotient rounds to k and
+    // rem is the delta the division would give; otherwise (near a tie, or
+    // not finite) the division decides.
+    const double inv = 1.0 / (double)D1;
     long long mi[D1];
     double delta[D1];
     bool ok = true;
 #pragma unroll
     for (int i = 0; i < D1; ++i) {
-        double q = rint(__ddiv_rn(x[i], (double)D1));
+        double q = rint(__dmul_rn(x[i], inv));
+        double rem = __dsub_rn(x[i], __dmul_rn((double)D1, q));
+        const double thr = (double)D1 * (0.5 - 0x1p-50 * (fabs(q) + 2.0));
+        if (!(fabs(rem) <= thr)) {
+            q = rint(__ddiv_rn(x[i], (double)D1));
+            rem = __dsub_rn(x[i], __dmul_rn((double)D1, q));
+        }
         if (!(fabs(q) < 1.0e12)) ok = false;   // also catches NaN
         mi[i] = ok ? (long long)q : 0;
-        delta[i] = __dsub_rn(x[i], __dmul_rn((double)D1, q));
+        delta[i] = rem;
     }
     if (!ok) {
         dcrf_flag(status, DCRF_E_NONFINITE);
@@ -199,13 +213,22 @@ __global__ void k_embed_insert(const float *__restrict__ feat, int64_t n, EmbedP
         for (int k = 0; k < D1; ++k) { pslot[a * D1 + k] = -1; pbary[a * D1 + k] = 0.f; }
         return;
     }
+    // ranks by delta, descending, ties by index: compared as integers (the
+    // FP64 order of finite values, -0 taken as +0), which keeps the 2 (d+1)^2
+    // comparisons off the FP64 pipe
+    long long dk[D1];
+#pragma unroll
+    for (int i = 0; i < D1; ++i) {
+        const long long bits = __double_as_longlong(delta[i] + 0.0);
+        dk[i] = bits < 0 ? bits ^ 0x7fffffffffffffffll : bits;
+    }
     int rank[D1];
 #pragma unroll
     for (int i = 0; i < D1; ++i) {
         int r = 0;
 #pragma unroll
         for (int j = 0; j < D1; ++j)
-            r += (delta[j] > delta[i]) || (delta[j] == delta[i] && j < i);
+            r += (dk[j] > dk[i]) || (dk[j] == dk[i] && j < i);
         rank[i] = r;
     }
     long long s = 0;
@@ -234,10 +257,12 @@ __global__ void k_embed_insert(const float *__restrict__ feat, int64_t n, EmbedP
         for (int p = 0; p < D1; ++p)
             if (rank[i] == p) ys[p] = dl;
     }
+    // barycentric weights: differences times RN(1/(d+1)) (within an FP64 ulp
+    // of the quotient; the weights are stored as float32)
     double b[D1];
 #pragma unroll
-    for (int k = 1; k < D1; ++k) b[k] = __ddiv_rn(__dsub_rn(ys[D - k], ys[D + 1 - k]), (double)D1);
-    b[0] = __dsub_rn(1.0, __ddiv_rn(__dsub_rn(ys[0], ys[D]), (double)D1));
+    for (int k = 1; k < D1; ++k) b[k] = __dmul_rn(__dsub_rn(ys[D - k], ys[D + 1 - k]), inv);
+    b[0] = __dsub_rn(1.0, __dmul_rn(__dsub_rn(ys[0], ys[D]), inv));
 
     const int64_t base = tab_base[img];
     const uint64_t mask = (uint64_t)tab_mask[img];
