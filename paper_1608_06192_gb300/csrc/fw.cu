@@ -575,12 +575,12 @@ __global__ void k_fw_latupd(FwLats F, UpdArgs U) {
 #pragma unroll
     for (int k = 1; k < DCRF_MAX_KERNELS; ++k)
         if (k == mm) { BY = F.l[k].BY; BS = F.l[k].BS; BYh = F.l[k].BYh; vimg = F.l[k].vimg; }
-    int64_t start = U.start[0], end = U.start[1];
+    int64_t start = U.start[0];
 #pragma unroll
     for (int k = 1; k < DCRF_MAX_KERNELS; ++k)
-        if (k == mm) { start = U.start[k]; end = U.start[k + 1]; }
+        if (k == mm) start = U.start[k];
     const int64_t idx = g - start;
-    const float al = (float)U.alpha[vimg[dcrf_div(idx, U.G, end - start)]];
+    const float al = (float)U.alpha[vimg[idx / U.G]];
     float4 by = ld4(BY, idx);
     const float4 bs = ld4((const T *)BS, idx);
     by.x += al * (bs.x - by.x); by.y += al * (bs.y - by.y); by.z += al * (bs.z - by.z); by.w += al * (bs.w - by.w);
