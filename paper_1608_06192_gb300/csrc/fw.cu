@@ -620,24 +620,46 @@ __global__ void k_fw_check_y(const float *__restrict__ Y, int64_t n, int L, int 
 // 64-bit integer reduction (low and high word; a word's sum stays below 2^32,
 // since 0 <= y <= 1 bounds it by 2^k (S 1)_v + the roundings, so no carry
 // crosses into the other label).
+// D1C > 0: d+1 fixed at compile time, every corner's vertex id and weight
+// loaded before the first reduction (the loop over runtime d+1 waited on each
+// corner's loads in turn).
+template <int D1C>
 __global__ void k_fw_splat_y0(const float *__restrict__ Y, int64_t n, int L, int Lp, int D1,
                               const int32_t *__restrict__ pvid, const float *__restrict__ pbary, const float *qs,
                               uint32_t *Sq) {
     const int H = Lp >> 1;
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= n * H) return;
-    const int64_t a = dcrf_div(idx, H, n * H);
+    const int64_t a = idx / H;
     const int c0 = 2 * (int)(idx - a * H);
     const float q = __ldg(qs);
     const float y0 = c0 < L ? fmaxf(Y[a * L + c0], 0.f) : 0.f;
     const float y1 = c0 + 1 < L ? fmaxf(Y[a * L + c0 + 1], 0.f) : 0.f;
-    for (int k = 0; k < D1; ++k) {
-        const int v = pvid[a * D1 + k];
-        if (v < 0) continue;
-        const float w = q * pbary[a * D1 + k];
-        const unsigned long long lo = __float2uint_rn(w * y0), hi = __float2uint_rn(w * y1);
-        if (lo | hi)
-            atomicAdd(reinterpret_cast<unsigned long long *>(Sq + (int64_t)v * Lp + c0), lo | (hi << 32));
+    if constexpr (D1C > 0) {
+        int v[D1C];
+        float w[D1C];
+#pragma unroll
+        for (int k = 0; k < D1C; ++k) {
+            v[k] = pvid[a * D1C + k];
+            w[k] = pbary[a * D1C + k];
+        }
+#pragma unroll
+        for (int k = 0; k < D1C; ++k) {
+            if (v[k] < 0) continue;
+            const float wq = q * w[k];
+            const unsigned long long lo = __float2uint_rn(wq * y0), hi = __float2uint_rn(wq * y1);
+            if (lo | hi)
+                atomicAdd(reinterpret_cast<unsigned long long *>(Sq + (int64_t)v[k] * Lp + c0), lo | (hi << 32));
+        }
+    } else {
+        for (int k = 0; k < D1; ++k) {
+            const int v = pvid[a * D1 + k];
+            if (v < 0) continue;
+            const float w = q * pbary[a * D1 + k];
+            const unsigned long long lo = __float2uint_rn(w * y0), hi = __float2uint_rn(w * y1);
+            if (lo | hi)
+                atomicAdd(reinterpret_cast<unsigned long long *>(Sq + (int64_t)v * Lp + c0), lo | (hi << 32));
+        }
     }
 }
 
@@ -911,8 +933,13 @@ struct Solver {
             DCRF_TRY(cudaMemsetAsync(l.Sq, 0, cnt * sizeof(uint32_t), s));
             if (n > 0 && l.m > 0) {
                 ProfScope ps(P_SPLAT_DENSE, s);
-                k_fw_splat_y0<<<nblocks(n * (Lp / 2), 256), 256, 0, s>>>(Y, n, L, Lp, l.d1, l.pvid, l.pbary, l.qs,
-                                                                         l.Sq);
+                const unsigned gb = nblocks(n * (Lp / 2), 256);
+                if (l.d1 == 6)
+                    k_fw_splat_y0<6><<<gb, 256, 0, s>>>(Y, n, L, Lp, l.d1, l.pvid, l.pbary, l.qs, l.Sq);
+                else if (l.d1 == 3)
+                    k_fw_splat_y0<3><<<gb, 256, 0, s>>>(Y, n, L, Lp, l.d1, l.pvid, l.pbary, l.qs, l.Sq);
+                else
+                    k_fw_splat_y0<0><<<gb, 256, 0, s>>>(Y, n, L, Lp, l.d1, l.pvid, l.pbary, l.qs, l.Sq);
                 DCRF_LAUNCHED();
                 k_fw_dequant<<<nblocks(l.m * Lp / 4, 256), 256, 0, s>>>(l.Sq, l.m * Lp / 4, l.qs, l.Ylat);
                 DCRF_LAUNCHED();
