@@ -28,7 +28,12 @@ def test_static_scratch_filter_matches_allocating_filter(dcrf):
     p = S.make_problem(160, 120, 10, 21, seed=77)
     g = gpu_setup(dcrf, [p], torch)
     rng = np.random.default_rng(5)
-    for storage, tol in (("f32", 1e-4), ("f16", 2e-3)):
+    # both entry points run the same splat, blur and slice kernels; the dense
+    # splat adds float32 values with atomics, so two calls of the allocating
+    # filter differ by as much as these two (measured on 160x120, L=21:
+    # 4.6e-7 in float32, and 8.2e-4 in float16 storage, where a changed last
+    # bit of a splat sum can flip the rounding of a stored half)
+    for storage, tol in (("f32", 1e-5), ("f16", 2e-3)):
         for call in range(2):                      # two calls in a row share the array
             Y = torch.from_numpy(rng.uniform(0, 1, (p.n_pixels, 21)).astype(np.float32)).cuda()
             for lat in (g["lb"], g["ls"]):
