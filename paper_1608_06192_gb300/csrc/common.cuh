@@ -170,7 +170,6 @@ __device__ __forceinline__ int64_t dcrf_div(int64_t idx, int cols, int64_t count
 // (exclusive) or in[0 .. i] (inclusive); out may not alias in.
 dcrf_status dcrf_scan(const int32_t *in, int32_t *out, int64_t n, bool inclusive, cudaStream_t s);
 dcrf_status dcrf_scan(const uint32_t *in, int64_t *out, int64_t n, bool inclusive, cudaStream_t s);
-dcrf_status dcrf_scan(const int32_t *in, int64_t *out, int64_t n, bool inclusive, cudaStream_t s);
 // Looks up, once per device, the device address of dcrf_filter_static's
 // array for the device of stream s (noalloc.cu).
 dcrf_status dcrf_static_scratch(cudaStream_t s, unsigned char **out);

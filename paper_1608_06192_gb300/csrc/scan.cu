@@ -117,6 +117,3 @@ dcrf_status dcrf_scan(const int32_t *in, int32_t *out, int64_t n, bool inclusive
 dcrf_status dcrf_scan(const uint32_t *in, int64_t *out, int64_t n, bool inclusive, cudaStream_t s) {
     return scan_impl<uint32_t, int64_t>(in, out, n, inclusive, s);
 }
-dcrf_status dcrf_scan(const int32_t *in, int64_t *out, int64_t n, bool inclusive, cudaStream_t s) {
-    return scan_impl<int32_t, int64_t>(in, out, n, inclusive, s);
-}
