@@ -186,11 +186,13 @@ __global__ void k_embed_insert(const float *__restrict__ feat, int64_t n, EmbedP
     // delta_i = x_i - (d+1) m_i, as the correctly rounded quotient gives them,
     // without the FP64 division where that is provable (FP64 throughput bounds
     // this kernel).  With k = rint(x RN(1/(d+1))) and rem = RN(x - (d+1) k),
-    // |RN(x/(d+1)) - k| <= |rem|/(d+1) + 2^-53 (|k| + 2), so when
-    // |rem| <= (d+1) (1/2 - 2^-50 (|k| + 2)) the quotient rounds to k and
-    // rem is the delta the division would give; otherwise (near a tie, or
-    // not finite) the division decides.
+    // |RN(x/(d+1)) - k| <= |rem|/(d+1) + 2^-53 (|k| + 2) < |rem|/(d+1) + 2^-13
+    // for |k| < 2^40 (larger k fail the 1e12 range check below whichever way
+    // they are found), so when |rem| <= 0.499 (d+1) the quotient rounds to k
+    // and rem is the delta the division would give; otherwise (near a tie,
+    // or not finite) the division decides.
     const double inv = 1.0 / (double)D1;
+    constexpr double thr = 0.499 * D1;
     long long mi[D1];
     double delta[D1];
     bool ok = true;
@@ -198,7 +200,6 @@ __global__ void k_embed_insert(const float *__restrict__ feat, int64_t n, EmbedP
     for (int i = 0; i < D1; ++i) {
         double q = rint(__dmul_rn(x[i], inv));
         double rem = __dsub_rn(x[i], __dmul_rn((double)D1, q));
-        const double thr = (double)D1 * (0.5 - 0x1p-50 * (fabs(q) + 2.0));
         if (!(fabs(rem) <= thr)) {
             q = rint(__ddiv_rn(x[i], (double)D1));
             rem = __dsub_rn(x[i], __dmul_rn((double)D1, q));
@@ -234,16 +235,19 @@ __global__ void k_embed_insert(const float *__restrict__ feat, int64_t n, EmbedP
     long long s = 0;
 #pragma unroll
     for (int i = 0; i < D1; ++i) s += mi[i];
+    bool moved[D1];
+#pragma unroll
+    for (int i = 0; i < D1; ++i) moved[i] = false;
     if (s > 0) {
 #pragma unroll
         for (int i = 0; i < D1; ++i) {
-            if (rank[i] >= D1 - s) { mi[i] -= 1; rank[i] -= (int)(D1 - s); }
+            if (rank[i] >= D1 - s) { mi[i] -= 1; rank[i] -= (int)(D1 - s); moved[i] = true; }
             else rank[i] += (int)s;
         }
     } else if (s < 0) {
 #pragma unroll
         for (int i = 0; i < D1; ++i) {
-            if (rank[i] < -s) { mi[i] += 1; rank[i] += (int)(D1 + s); }
+            if (rank[i] < -s) { mi[i] += 1; rank[i] += (int)(D1 + s); moved[i] = true; }
             else rank[i] += (int)s;
         }
     }
@@ -252,7 +256,8 @@ __global__ void k_embed_insert(const float *__restrict__ feat, int64_t n, EmbedP
     for (int p = 0; p < D1; ++p) ys[p] = 0.0;
 #pragma unroll
     for (int i = 0; i < D1; ++i) {
-        double dl = __dsub_rn(x[i], __dmul_rn((double)D1, (double)mi[i]));
+        // the remainder of an unmoved coordinate is the one computed above
+        const double dl = moved[i] ? __dsub_rn(x[i], __dmul_rn((double)D1, (double)mi[i])) : delta[i];
 #pragma unroll
         for (int p = 0; p < D1; ++p)
             if (rank[i] == p) ys[p] = dl;
